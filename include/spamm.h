@@ -1,0 +1,187 @@
+/*
+ * spamm.h -- C ABI of the GB300 (sm_103a) implementation of sparse approximate
+ * matrix-matrix multiplication (SpAMM) with strict error control and its use in
+ * SP2 density-matrix purification (Artemov & Rubensson, "Sparse approximate
+ * matrix-matrix multiplication for density matrix purification with error
+ * control").
+ *
+ * Conventions for every entry point:
+ *   - Return value: 0 (SPAMM_OK) or one of the SPAMM_E* codes below; the text
+ *     of the last failure on the calling thread is spamm_last_error().
+ *   - All GPU work is ordered on the context's CUDA stream. Calls return after
+ *     the scalars they report are on the host.
+ *   - Matrices (spamm_mat) are square, float64, stored on the context's device
+ *     as a list of bs x bs leaf blocks (row-major inside a block) with a dense
+ *     nb x nb block map, nb = ceil(n / bs). A block that is absent from the map
+ *     is identically zero (the zero-flagged quadtree nodes of Eq. 2); the
+ *     quadtree of Eq. 2 over the padded size bs * 2^L >= n is implicit in the
+ *     block coordinates. Blocks that straddle n are zero-padded.
+ *   - Objects returned through a pointer-to-pointer are owned by the caller
+ *     and released with the matching *_free / *_destroy call. Inputs are never
+ *     modified except by spamm_truncate.
+ */
+#ifndef SPAMM_GB300_H
+#define SPAMM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPAMM_OK 0
+#define SPAMM_EINVAL 1       /* bad argument: shape, NaN, delta <= 0, n_occ out of range */
+#define SPAMM_ENOMEM 2       /* device allocation failed */
+#define SPAMM_ECUDA 3        /* a CUDA call failed; spamm_last_error() has its text */
+#define SPAMM_ETIMEOUT 4     /* a bounded device-side wait gave up */
+#define SPAMM_ENOTCONV 5     /* purification hit n_iter before the stop rule */
+#define SPAMM_ENOTSUP 6      /* parameter combination not supported by this build */
+
+#define SPAMM_N_TAU 350      /* tau candidates: tau_1 = 1, tau_i = 0.9 tau_{i-1} */
+
+typedef struct spamm_ctx spamm_ctx;
+typedef struct spamm_mat spamm_mat;
+
+/* Leaf-product arithmetic. FP64: every kept leaf product in float64.
+   MIXED: leaf products on the bf16 tensor cores via exact fixed-point
+   slices; the slicing error is bounded per kept product and charged inside
+   the Algorithm 3 bound, so the certified bound still covers the result. */
+typedef enum { SPAMM_FP64 = 0, SPAMM_MIXED = 1 } spamm_prec;
+
+/* Purification variants, numbered as the paper's algorithms:
+   1 = multiply exactly then truncate (Algorithm 1, "truncmul"),
+   4 = SpAMM with error control only (Algorithm 4),
+   5 = SpAMM at delta_i/2 then truncation at delta_i/2 (Algorithm 5, hybrid). */
+typedef enum { SPAMM_TRUNCMUL = 1, SPAMM_APPROX = 4, SPAMM_HYBRID = 5 } spamm_variant;
+
+/* Phase timers (milliseconds, CUDA events) in spamm_report.ms[]. */
+enum { SPAMM_T_NORMS = 0, SPAMM_T_CSE = 1, SPAMM_T_PLAN = 2, SPAMM_T_GEMM = 3,
+       SPAMM_T_TRUNC = 4, SPAMM_T_SPLIT = 5, SPAMM_T_TOTAL = 6 };
+
+typedef struct {
+    double tau;            /* SpAMM threshold used; 0 means the exact product */
+    int32_t tau_index;     /* 0-based index into the candidate table, -1 if none */
+    int32_t cse_evals;     /* Algorithm 3 evaluations run by the tau search */
+    double bound;          /* certified ||SpAMM(A,B,tau) - AB||_F bound (Alg. 3), incl. bound_round */
+    double bound_round;    /* part of bound charged for mixed-precision leaf products */
+    int64_t candidates;    /* leaf triples (i,k,j) with A_ik and B_kj both present */
+    int64_t kept;          /* leaf products formed (p >= tau) */
+    int64_t nnzb_out;      /* leaf blocks in the result */
+    double fro_out;        /* ||result||_F */
+    double trace_out;      /* trace of the result */
+    double idem;           /* spamm_sp2_step only: ||X^2 (approx) - X||_F */
+    double removed_sq;     /* spamm_truncate: sum of removed ||block||_F^2 (upper bound) */
+    int64_t removed_blocks;/* spamm_truncate: leaf blocks removed */
+    float ms[8];           /* phase times, indexed by SPAMM_T_* */
+} spamm_report;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
+   owned by the caller, or NULL to let the context create (and own) one. */
+int spamm_create(spamm_ctx** ctx, int device, void* cuda_stream);
+void spamm_destroy(spamm_ctx* ctx);
+const char* spamm_strerror(int status);
+const char* spamm_last_error(void);
+
+/* --------------------------------------------------------------- matrices */
+
+/* Build a block-sparse matrix from a dense n x n row-major array (leading
+   dimension ld >= n), host or device memory as `a_on_device` says. Entries
+   with |x| < drop_abs become zero; a leaf block whose entries are all zero is
+   not stored. bs must be 32, 64 or 128. */
+int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, int64_t ld, int bs,
+                         double drop_abs, int a_on_device, spamm_mat** out);
+
+/* Write the matrix densely into out (n x n, leading dimension ld), host or
+   device memory as `out_on_device` says. */
+int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* out, int64_t ld,
+                       int out_on_device);
+
+/* Shape and storage: any pointer may be NULL. */
+int spamm_mat_info(const spamm_mat* m, int64_t* n, int* bs, int64_t* nnzb);
+
+/* Leaf-block Frobenius norms into host array out[nb*nb] (0 for absent blocks). */
+int spamm_mat_block_norms(spamm_ctx* ctx, const spamm_mat* m, double* out);
+
+/* Block map into host array out[nb*nb]: 1 where the leaf block is stored, else 0. */
+int spamm_mat_block_map(spamm_ctx* ctx, const spamm_mat* m, int32_t* out);
+
+void spamm_mat_free(spamm_mat* m);
+
+/* ------------------------------------------------------------ operations */
+
+/* Algorithm 3 (CSE): the error bound of SpAMM(A, B, taus[t]) for each of the N
+   candidates, into host array errors[N]. taus is a host array. */
+int spamm_cse(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* taus,
+              int N, double* errors);
+
+/* spamm(A, B, delta) -> C with ||C - AB||_F < delta (problem statement after
+   Algorithm 2): choose tau as the candidate whose Algorithm 3 bound is the
+   largest one below delta (the bound is non-increasing along the table, so a
+   bisection finds it), then form Algorithm 2's product. If no candidate's
+   bound is below delta the exact product is formed (tau = 0). */
+int spamm_multiply(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double delta,
+                   spamm_prec prec, spamm_mat** C, spamm_report* rep);
+
+/* Algorithm 2 with a given threshold: C = sum of A_ik B_kj over leaf triples
+   with ||A_ik||_F ||B_kj||_F >= tau (tau = 0: the exact product). */
+int spamm_multiply_tau(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double tau,
+                       spamm_prec prec, spamm_mat** C, spamm_report* rep);
+
+/* One SP2 step on a symmetric X: C ~ X^2 by spamm(X, X, delta) (tau >= 0 given
+   instead when delta <= 0 and tau >= 0), then Xn = C (branch 0) or
+   Xn = 2X - C (branch 1), the polynomials f_i of Algorithms 1, 4 and 5.
+   rep->idem = ||C - X||_F; rep->trace_out = tr(Xn). */
+int spamm_sp2_step(spamm_ctx* ctx, const spamm_mat* X, int branch, double delta, double tau,
+                   spamm_prec prec, spamm_mat** Xn, spamm_report* rep);
+
+/* Truncation ||E||_F < delta (Algorithm 1, the E_i step), in place, on leaf
+   blocks: the units (a diagonal block, or the pair X_ij, X_ji when symmetric
+   != 0; single blocks otherwise) are ordered by squared norm and the longest
+   prefix whose summed squared norm stays below delta^2 is removed. */
+int spamm_truncate(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric,
+                   spamm_report* rep);
+
+/* ------------------------------------------------------------ purification */
+
+typedef struct {
+    spamm_variant variant;   /* 1, 4 or 5 */
+    spamm_prec prec;
+    double homo;             /* upper bound of the n_occ-th smallest eigenvalue of F */
+    double lumo;             /* lower bound of the (n_occ+1)-th smallest eigenvalue */
+    int have_bounds;         /* 1: lmin/lmax below are spectral bounds of F; 0: Gershgorin */
+    double lmin, lmax;
+} spamm_purify_opts;
+
+typedef struct {
+    int32_t iters;           /* accepted SP2 steps */
+    int32_t converged;       /* 1 when the stop rule fired */
+    double idem;             /* last ||X^2 - X||_F estimate (+ its multiply bound) */
+    double trace;            /* trace of the returned D */
+    double lmin, lmax;       /* spectral bounds used for X_0 */
+    int64_t kept_total;      /* leaf products formed over all steps */
+    int64_t cand_total;      /* leaf triples considered over all steps */
+    double ms_total;         /* wall time of the purification (CUDA events) */
+    double ms_phase[8];      /* phase totals, indexed by SPAMM_T_* */
+    /* optional per-step logs (caller-owned host arrays of length n_iter, or NULL) */
+    double* step_delta;
+    double* step_tau;
+    double* step_trace;
+    double* step_idem;
+    int32_t* step_branch;    /* 0: X^2, 1: 2X - X^2 */
+    int64_t* step_nnzb;
+} spamm_purify_report;
+
+/* SP2 purification of F (symmetric) with error control so that
+   ||D - D~||_F < eps (Algorithms 1, 4, 5 with the f_i of SP2). homo/lumo
+   (a gap at n_occ) are required: the per-step tolerances delta_i depend on it.
+   D is returned (caller frees). SPAMM_ENOTCONV when n_iter steps did not
+   satisfy the stop rule (D and the report are still filled). */
+int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, double eps, int n_iter,
+                 const spamm_purify_opts* opts, spamm_mat** D, spamm_purify_report* rep);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,511 @@
+// C ABI entry points: context, spamm(A, B, delta), Algorithm 2 with a given
+// tau, one SP2 step, truncation and the purification driver (Algorithms 1, 4
+// and 5 with the SP2 polynomials).
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace spamm {
+int mixed_available();
+int gemm_mixed(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const Plan& plan,
+               const Epilogue& ep, spamm_mat* C, double* d_part_fro2, double* d_part_trace,
+               double* d_part_idem2);
+}
+
+using namespace spamm;
+
+namespace {
+
+enum { EV_T0 = 0, EV_CSE0, EV_CSE1, EV_PLAN1, EV_GEMM1, EV_END, EV_TR0, EV_TR1 };
+
+__global__ void k_select_tau(DevScalars* sc, const double* __restrict__ tau, int N) {
+    sc->tau_sel = sc->hi < N ? tau[sc->hi] : 0.0;
+}
+
+__global__ void k_set_tau(DevScalars* sc, double tau) { sc->tau_sel = tau; }
+
+int check_pair(const spamm_mat* A, const spamm_mat* B) {
+    if (!A || !B || A->n != B->n || A->bs != B->bs) {
+        set_error("operands must have the same n and bs");
+        return SPAMM_EINVAL;
+    }
+    return SPAMM_OK;
+}
+
+float ev_ms(spamm_ctx* ctx, int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]);
+    return ms;
+}
+
+// Shared body of spamm_multiply, spamm_multiply_tau and spamm_sp2_step.
+//   search: run the tau bisection for `delta`; else use `tau`.
+//   mode: 0 plain product, 1 SP2 X^2 branch, 2 SP2 2X - X^2 branch (A = B = X).
+int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool search,
+                  double delta, double tau, spamm_prec prec, int mode, spamm_mat** Cout,
+                  spamm_report* rep) {
+    SP_TRY(check_pair(A, B));
+    if (prec != SPAMM_FP64 && prec != SPAMM_MIXED) {
+        set_error("unknown precision %d", (int)prec);
+        return SPAMM_EINVAL;
+    }
+    if (prec == SPAMM_MIXED && !mixed_available()) {
+        set_error("mixed-precision leaf products are not built for this bs/device");
+        return SPAMM_ENOTSUP;
+    }
+    SP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    DevScalars* sc = (DevScalars*)ctx->d_scalars;
+    spamm_report r;
+    memset(&r, 0, sizeof r);
+    cudaEventRecord(ctx->ev[EV_T0], s);
+    int evals = 0;
+    if (search) {
+        SP_TRY(cse_search(ctx, A, B, delta, nullptr, &evals));
+        k_select_tau<<<1, 1, 0, s>>>(sc, ctx->d_tau, SPAMM_N_TAU);
+    } else {
+        k_set_tau<<<1, 1, 0, s>>>(sc, tau);
+        SP_TRY(cse_eval(ctx, A, B, &sc->tau_sel, &sc->err_at_hi, nullptr));
+        evals = 1;
+    }
+    SP_CHECK_LAUNCH();
+    cudaEventRecord(ctx->ev[EV_CSE1], s);
+    Plan plan;
+    spamm_mat* C = nullptr;
+    SP_TRY(plan_build_impl(ctx, A, B, &sc->tau_sel, mode ? A : nullptr, mode == 2, &plan, &C));
+    cudaEventRecord(ctx->ev[EV_PLAN1], s);
+    double* parts = nullptr;
+    int64_t nw = plan.n_work > 0 ? plan.n_work : 1;
+    int st = dalloc((void**)&parts, sizeof(double) * 3 * nw, s);
+    if (st == SPAMM_OK) {
+        Epilogue ep{mode, mode ? A : nullptr};
+        if (prec == SPAMM_FP64)
+            st = gemm_fp64(ctx, A, B, plan, ep, C, parts, parts + nw, parts + 2 * nw);
+        else
+            st = gemm_mixed(ctx, A, B, plan, ep, C, parts, parts + nw, parts + 2 * nw);
+    }
+    cudaEventRecord(ctx->ev[EV_GEMM1], s);
+    if (st == SPAMM_OK) {
+        if (plan.n_work > 0)
+            st = reduce_partials(ctx, parts, parts + nw, parts + 2 * nw, plan.n_work);
+        else
+            st = cudaMemsetAsync(&sc->fro2, 0, 3 * sizeof(double), s) == cudaSuccess ? SPAMM_OK
+                                                                                     : SPAMM_ECUDA;
+    }
+    cudaEventRecord(ctx->ev[EV_END], s);
+    DevScalars h;
+    if (st == SPAMM_OK) {
+        cudaError_t e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "report copy", __FILE__, __LINE__);
+    }
+    const int64_t n_cand = plan.n_cand, n_tasks = plan.n_tasks;
+    dfree(parts, s);
+    plan_free(&plan, s);
+    if (st != SPAMM_OK) {
+        spamm_mat_free(C);
+        return st;
+    }
+    r.tau = h.tau_sel;
+    r.tau_index = search ? (h.hi < SPAMM_N_TAU ? h.hi : -1) : -1;
+    r.cse_evals = evals;
+    r.bound = (search && h.hi >= SPAMM_N_TAU) ? 0.0 : h.err_at_hi;
+    r.bound_round = 0.0;
+    r.candidates = n_cand;
+    r.kept = n_tasks;
+    r.nnzb_out = C->nnzb;
+    r.fro_out = std::sqrt(h.fro2);
+    r.trace_out = h.trace;
+    r.idem = std::sqrt(h.idem2);
+    r.ms[SPAMM_T_CSE] = ev_ms(ctx, EV_T0, EV_CSE1);
+    r.ms[SPAMM_T_PLAN] = ev_ms(ctx, EV_CSE1, EV_PLAN1);
+    r.ms[SPAMM_T_GEMM] = ev_ms(ctx, EV_PLAN1, EV_GEMM1);
+    r.ms[SPAMM_T_TOTAL] = ev_ms(ctx, EV_T0, EV_END);
+    if (rep) *rep = r;
+    *Cout = C;
+    return SPAMM_OK;
+}
+
+// ---- purification helpers
+
+// Gershgorin bounds: one CTA per block row, one thread per row of the block row.
+__global__ void k_gershgorin(const double* __restrict__ tiles, const int32_t* __restrict__ map,
+                             int nb, int bs, int64_t n, double* __restrict__ lo_part,
+                             double* __restrict__ hi_part) {
+    const int bi = blockIdx.x;
+    const int r = threadIdx.x;
+    const int64_t row = (int64_t)bi * bs + r;
+    double absum = 0.0, diag = 0.0;
+    for (int bj = 0; bj < nb; ++bj) {
+        const int32_t s = map[(int64_t)bi * nb + bj];
+        if (s < 0) continue;
+        const double* t = tiles + (int64_t)s * bs * bs + (int64_t)r * bs;
+        for (int c = 0; c < bs; ++c) {
+            const double x = t[c];
+            if (bj == bi && c == r) diag = x;
+            else absum += fabs(x);
+        }
+    }
+    double lo = INFINITY, hi = -INFINITY;
+    if (row < n) {
+        lo = diag - absum;
+        hi = diag + absum;
+    }
+    __shared__ double sl[128], sh[128];
+    sl[r] = lo;
+    sh[r] = hi;
+    __syncthreads();
+    if (r == 0) {
+        for (int q = 1; q < bs; ++q) {
+            lo = fmin(lo, sl[q]);
+            hi = fmax(hi, sh[q]);
+        }
+        lo_part[bi] = lo;
+        hi_part[bi] = hi;
+    }
+}
+
+__global__ void k_minmax(const double* lo_part, const double* hi_part, int nb, double* out) {
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = 0; i < nb; ++i) {
+        lo = fmin(lo, lo_part[i]);
+        hi = fmax(hi, hi_part[i]);
+    }
+    out[0] = lo;
+    out[1] = hi;
+}
+
+// X_0 = (lmax I - F) / (lmax - lmin): pattern of F plus every diagonal block.
+__global__ void k_x0_flags(const int32_t* __restrict__ mapF, int nb, int32_t* flag) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)nb * nb) return;
+    flag[b] = (mapF[b] >= 0 || (b / nb) == (b % nb)) ? 1 : 0;
+}
+
+__global__ void k_x0_fill(const double* __restrict__ tilesF, const int32_t* __restrict__ mapF,
+                          const int32_t* __restrict__ flag, const int64_t* __restrict__ slot,
+                          int nb, int bs, int64_t n, double lmax, double width,
+                          int32_t* __restrict__ map, int32_t* __restrict__ coord,
+                          double* __restrict__ tiles) {
+    const int64_t b = blockIdx.x;
+    if (!flag[b]) return;
+    const int bi = (int)(b / nb), bj = (int)(b % nb);
+    const int64_t s = slot[b];
+    const int32_t sf = mapF[b];
+    double* t = tiles + s * (int64_t)bs * bs;
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+        const int r = e / bs, c = e % bs;
+        double x = sf >= 0 ? -tilesF[(int64_t)sf * bs * bs + e] / width : 0.0;
+        if (bi == bj && r == c && (int64_t)bi * bs + r < n) x += lmax / width;
+        t[e] = x;
+    }
+    if (threadIdx.x == 0) {
+        map[b] = (int32_t)s;
+        coord[s] = (int32_t)b;
+    }
+}
+
+int make_x0(spamm_ctx* ctx, const spamm_mat* F, double lmin, double lmax, spamm_mat** out) {
+    cudaStream_t s = ctx->stream;
+    const int nb = F->nb;
+    const int64_t nb2 = (int64_t)nb * nb;
+    int32_t* flag = nullptr;
+    int64_t* slot = nullptr;
+    unsigned long long* tot = nullptr;
+    SP_TRY(dalloc((void**)&flag, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&slot, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&tot, 8, s));
+    k_x0_flags<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(F->d_map, nb, flag);
+    SP_TRY(scan_i32_to_i64(ctx, flag, slot, nb2, tot));
+    unsigned long long cnt = 0;
+    SP_CUDA(cudaMemcpyAsync(&cnt, tot, 8, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    spamm_mat* X = nullptr;
+    SP_TRY(mat_alloc(ctx, F->n, F->bs, (int64_t)cnt, &X));
+    X->nslots = X->nnzb = (int64_t)cnt;
+    k_x0_fill<<<(unsigned)nb2, 256, 0, s>>>(F->d_tiles, F->d_map, flag, slot, nb, F->bs, F->n,
+                                            lmax, lmax - lmin, X->d_map, X->d_coord, X->d_tiles);
+    SP_CHECK_LAUNCH();
+    SP_TRY(mat_compute_norms(ctx, X));
+    dfree(flag, s);
+    dfree(slot, s);
+    dfree(tot, s);
+    *out = X;
+    return SPAMM_OK;
+}
+
+int read_trace(spamm_ctx* ctx, const spamm_mat* X, double* tr) {
+    DevScalars* sc = (DevScalars*)ctx->d_scalars;
+    SP_TRY(mat_trace(ctx, X, &sc->trace));
+    SP_CUDA(cudaMemcpyAsync(tr, &sc->trace, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    SP_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SPAMM_OK;
+}
+
+}  // namespace
+
+// ====================================================================== ABI
+
+extern "C" const char* spamm_strerror(int st) {
+    switch (st) {
+        case SPAMM_OK: return "ok";
+        case SPAMM_EINVAL: return "invalid argument";
+        case SPAMM_ENOMEM: return "out of device memory";
+        case SPAMM_ECUDA: return "CUDA error";
+        case SPAMM_ETIMEOUT: return "device-side wait timed out";
+        case SPAMM_ENOTCONV: return "purification did not converge within n_iter steps";
+        case SPAMM_ENOTSUP: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int spamm_create(spamm_ctx** out, int device, void* cuda_stream) {
+    if (!out) {
+        set_error("spamm_create: null output");
+        return SPAMM_EINVAL;
+    }
+    *out = nullptr;
+    int count = 0;
+    SP_CUDA(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count) {
+        set_error("spamm_create: device %d not present (%d devices)", device, count);
+        return SPAMM_EINVAL;
+    }
+    SP_CUDA(cudaSetDevice(device));
+    spamm_ctx* c = new spamm_ctx();
+    memset(c, 0, sizeof(*c));
+    c->device = device;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+        c->own_stream = false;
+    } else {
+        SP_CUDA(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+    SP_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+    // keep freed blocks in the stream-ordered pool
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    // tau_1 = 1, tau_i = 0.9 tau_{i-1}: repeated float64 multiplication
+    c->h_tau[0] = 1.0;
+    for (int i = 1; i < SPAMM_N_TAU; ++i) c->h_tau[i] = 0.9 * c->h_tau[i - 1];
+    SP_CUDA(cudaMalloc(&c->d_tau, sizeof(double) * SPAMM_N_TAU));
+    SP_CUDA(cudaMemcpy(c->d_tau, c->h_tau, sizeof(double) * SPAMM_N_TAU, cudaMemcpyHostToDevice));
+    SP_CUDA(cudaMalloc(&c->d_scalars, sizeof(DevScalars)));
+    SP_CUDA(cudaMemset(c->d_scalars, 0, sizeof(DevScalars)));
+    for (int i = 0; i < 12; ++i) SP_CUDA(cudaEventCreate(&c->ev[i]));
+    *out = c;
+    return SPAMM_OK;
+}
+
+extern "C" void spamm_destroy(spamm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 12; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    cudaFree(c->d_tau);
+    cudaFree(c->d_scalars);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+extern "C" int spamm_multiply(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double delta,
+                              spamm_prec prec, spamm_mat** C, spamm_report* rep) {
+    if (!ctx || !C || !(delta > 0.0) || !std::isfinite(delta)) {
+        set_error("spamm_multiply: need ctx, output and a finite delta > 0");
+        return SPAMM_EINVAL;
+    }
+    *C = nullptr;
+    return multiply_core(ctx, A, B, true, delta, 0.0, prec, 0, C, rep);
+}
+
+extern "C" int spamm_multiply_tau(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B,
+                                  double tau, spamm_prec prec, spamm_mat** C, spamm_report* rep) {
+    if (!ctx || !C || !(tau >= 0.0) || !std::isfinite(tau)) {
+        set_error("spamm_multiply_tau: need ctx, output and a finite tau >= 0");
+        return SPAMM_EINVAL;
+    }
+    *C = nullptr;
+    return multiply_core(ctx, A, B, false, 0.0, tau, prec, 0, C, rep);
+}
+
+extern "C" int spamm_sp2_step(spamm_ctx* ctx, const spamm_mat* X, int branch, double delta,
+                              double tau, spamm_prec prec, spamm_mat** Xn, spamm_report* rep) {
+    if (!ctx || !X || !Xn || (branch != 0 && branch != 1) || !std::isfinite(delta) ||
+        (!(delta > 0.0) && !(tau >= 0.0))) {
+        set_error("spamm_sp2_step: bad argument");
+        return SPAMM_EINVAL;
+    }
+    *Xn = nullptr;
+    bool search = delta > 0.0;
+    return multiply_core(ctx, X, X, search, delta, search ? 0.0 : tau, prec, branch == 0 ? 1 : 2,
+                         Xn, rep);
+}
+
+extern "C" int spamm_truncate(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric,
+                              spamm_report* rep) {
+    if (!ctx || !X || !(delta > 0.0) || !std::isfinite(delta)) {
+        set_error("spamm_truncate: need ctx, matrix and a finite delta > 0");
+        return SPAMM_EINVAL;
+    }
+    SP_CUDA(cudaSetDevice(ctx->device));
+    cudaEventRecord(ctx->ev[EV_TR0], ctx->stream);
+    int64_t removed = 0;
+    double rsq = 0.0;
+    SP_TRY(truncate_blocks(ctx, X, delta, symmetric, &removed, &rsq));
+    cudaEventRecord(ctx->ev[EV_TR1], ctx->stream);
+    if (rep) {
+        memset(rep, 0, sizeof(*rep));
+        double tr = 0.0;
+        SP_TRY(read_trace(ctx, X, &tr));
+        rep->removed_blocks = removed;
+        rep->removed_sq = rsq;
+        rep->nnzb_out = X->nnzb;
+        rep->trace_out = tr;
+        rep->ms[SPAMM_T_TRUNC] = ev_ms(ctx, EV_TR0, EV_TR1);
+    }
+    return SPAMM_OK;
+}
+
+extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, double eps,
+                            int n_iter, const spamm_purify_opts* opts, spamm_mat** D,
+                            spamm_purify_report* rep) {
+    if (!ctx || !F || !D || !opts || n_occ < 0 || n_occ > F->n || !(eps > 0.0) || n_iter <= 0 ||
+        !(opts->lumo > opts->homo) ||
+        (opts->variant != SPAMM_TRUNCMUL && opts->variant != SPAMM_APPROX &&
+         opts->variant != SPAMM_HYBRID)) {
+        set_error("spamm_purify: bad argument (need homo < lumo, eps > 0, 0 <= n_occ <= n)");
+        return SPAMM_EINVAL;
+    }
+    *D = nullptr;
+    SP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    spamm_purify_report R;
+    if (rep) R = *rep;
+    else memset(&R, 0, sizeof R);
+    R.iters = 0;
+    R.converged = 0;
+    R.kept_total = R.cand_total = 0;
+    for (int i = 0; i < 8; ++i) R.ms_phase[i] = 0.0;
+    cudaEvent_t e0, e1;
+    SP_CUDA(cudaEventCreate(&e0));
+    SP_CUDA(cudaEventCreate(&e1));
+    cudaEventRecord(e0, s);
+
+    double lmin = opts->lmin, lmax = opts->lmax;
+    if (!opts->have_bounds) {
+        double *part = nullptr, *mm = nullptr;
+        SP_TRY(dalloc((void**)&part, sizeof(double) * 2 * F->nb, s));
+        SP_TRY(dalloc((void**)&mm, sizeof(double) * 2, s));
+        k_gershgorin<<<F->nb, F->bs, 0, s>>>(F->d_tiles, F->d_map, F->nb, F->bs, F->n, part,
+                                             part + F->nb);
+        k_minmax<<<1, 1, 0, s>>>(part, part + F->nb, F->nb, mm);
+        SP_CHECK_LAUNCH();
+        double h[2];
+        SP_CUDA(cudaMemcpyAsync(h, mm, sizeof h, cudaMemcpyDeviceToHost, s));
+        SP_CUDA(cudaStreamSynchronize(s));
+        dfree(part, s);
+        dfree(mm, s);
+        lmin = h[0];
+        lmax = h[1];
+    }
+    if (!(lmax > lmin)) {
+        set_error("spamm_purify: degenerate spectral bounds");
+        return SPAMM_EINVAL;
+    }
+    R.lmin = lmin;
+    R.lmax = lmax;
+    const double width = lmax - lmin;
+    spamm_mat* X = nullptr;
+    SP_TRY(make_x0(ctx, F, lmin, lmax, &X));
+    // eigenvalue bounds in X units: occupied >= l, unoccupied <= h
+    double l = (lmax - opts->homo) / width;
+    double h = (lmax - opts->lumo) / width;
+    const double budget = eps / (2.0 * std::sqrt(2.0) * n_iter);
+    const int variant = opts->variant;
+    int st = SPAMM_OK;
+    if (variant == SPAMM_TRUNCMUL || variant == SPAMM_HYBRID) {
+        const double d0 = budget * (l - h);
+        spamm_report tr;
+        st = spamm_truncate(ctx, X, d0, 1, &tr);
+        R.ms_phase[SPAMM_T_TRUNC] += tr.ms[SPAMM_T_TRUNC];
+        h += d0;
+        l -= d0;
+    }
+    double trace = 0.0;
+    if (st == SPAMM_OK) st = read_trace(ctx, X, &trace);
+    double idem = 0.0;
+    for (int it = 1; it <= n_iter && st == SPAMM_OK; ++it) {
+        const bool sq = trace > (double)n_occ;
+        const double hn = sq ? h * h : 2 * h - h * h;
+        const double ln = sq ? l * l : 2 * l - l * l;
+        const double delta = budget * (ln - hn);
+        if (!(delta > 0.0)) {
+            set_error("spamm_purify: the propagated gap closed (step %d)", it);
+            st = SPAMM_EINVAL;
+            break;
+        }
+        spamm_report mr;
+        spamm_mat* Xn = nullptr;
+        if (variant == SPAMM_TRUNCMUL)
+            st = spamm_sp2_step(ctx, X, sq ? 0 : 1, 0.0, 0.0, opts->prec, &Xn, &mr);
+        else
+            st = spamm_sp2_step(ctx, X, sq ? 0 : 1, variant == SPAMM_APPROX ? delta : 0.5 * delta,
+                                0.0, opts->prec, &Xn, &mr);
+        if (st != SPAMM_OK) break;
+        R.kept_total += mr.kept;
+        R.cand_total += mr.candidates;
+        for (int q = 0; q < 8; ++q) R.ms_phase[q] += mr.ms[q];
+        idem = mr.idem + mr.bound;
+        if (2.0 * idem < 0.5 * eps) {
+            spamm_mat_free(Xn);
+            R.converged = 1;
+            break;
+        }
+        if (variant == SPAMM_TRUNCMUL || variant == SPAMM_HYBRID) {
+            spamm_report tr;
+            st = spamm_truncate(ctx, Xn, variant == SPAMM_TRUNCMUL ? delta : 0.5 * delta, 1, &tr);
+            if (st != SPAMM_OK) {
+                spamm_mat_free(Xn);
+                break;
+            }
+            R.ms_phase[SPAMM_T_TRUNC] += tr.ms[SPAMM_T_TRUNC];
+            trace = tr.trace_out;
+        } else {
+            trace = mr.trace_out;
+        }
+        h = hn + delta;
+        l = ln - delta;
+        const int k = R.iters;
+        if (R.step_delta) R.step_delta[k] = delta;
+        if (R.step_tau) R.step_tau[k] = mr.tau;
+        if (R.step_trace) R.step_trace[k] = trace;
+        if (R.step_idem) R.step_idem[k] = idem;
+        if (R.step_branch) R.step_branch[k] = sq ? 0 : 1;
+        if (R.step_nnzb) R.step_nnzb[k] = Xn->nnzb;
+        R.iters = it;
+        spamm_mat_free(X);
+        X = Xn;
+    }
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPAMM_OK) {
+        spamm_mat_free(X);
+        return st;
+    }
+    R.idem = idem;
+    R.trace = trace;
+    R.ms_total = ms;
+    if (rep) *rep = R;
+    *D = X;
+    return R.converged ? SPAMM_OK : SPAMM_ENOTCONV;
+}

@@ -1,0 +1,150 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string>
+
+#include "../../include/spamm.h"
+
+namespace spamm {
+
+// ----------------------------------------------------------------- errors
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define SP_CUDA(call)                                                         \
+    do {                                                                      \
+        cudaError_t _e = (call);                                              \
+        if (_e != cudaSuccess) return ::spamm::cuda_fail(_e, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define SP_CHECK_LAUNCH() SP_CUDA(cudaGetLastError())
+
+#define SP_TRY(call)                      \
+    do {                                  \
+        int _s = (call);                  \
+        if (_s != SPAMM_OK) return _s;    \
+    } while (0)
+
+}  // namespace spamm
+
+// ------------------------------------------------------------------ objects
+
+struct spamm_ctx {
+    int device;
+    cudaStream_t stream;
+    bool own_stream;
+    int num_sms;
+    double h_tau[SPAMM_N_TAU];
+    double* d_tau;               // tau table on the device
+    // device scalars used by the tau search and the reports
+    void* d_scalars;             // see struct DevScalars
+    void* h_scalars;             // pinned host mirror
+    cudaEvent_t ev[12];
+};
+
+struct spamm_mat {
+    int device;
+    cudaStream_t stream;         // stream the storage is ordered on
+    int64_t n;
+    int bs;
+    int nb;                      // ceil(n / bs)
+    int NB;                      // 2^L >= nb (implicit quadtree)
+    int64_t cap;                 // tile slots allocated
+    int64_t nslots;              // tile slots in use (some may be orphaned by truncation)
+    int64_t nnzb;                // live leaf blocks
+    int32_t* d_map;              // [nb*nb] slot or -1
+    int32_t* d_coord;            // [cap] i*nb+j of the slot, or -1 when orphaned
+    double* d_tiles;             // [cap*bs*bs]
+    double* d_norm;              // [nb*nb] ||X_ij||_F, 0 where absent
+    double* d_rowabs;            // optional scratch
+};
+
+namespace spamm {
+
+// Device scalars of one multiply/purification step (single struct so one copy
+// brings everything back to the host).
+struct DevScalars {
+    // tau bisection state
+    int32_t lo, hi, mid, done;
+    double tau_mid;
+    double tau_sel;                 // threshold used by the plan (0: exact product)
+    double err_mid;
+    double err_at_hi;
+    // plan counters
+    unsigned long long n_out;       // output blocks
+    unsigned long long n_tasks;     // kept leaf products
+    unsigned long long n_cand;      // candidate triples
+    // reductions
+    double fro2, trace, idem2, bound_round2;
+    // truncation
+    unsigned long long trunc_removed;
+    double trunc_removed_sq;
+    unsigned long long trunc_prefix;
+    unsigned long long trunc_below_sum;
+    int32_t trunc_digit_pass;
+    int32_t status;                  // nonzero: a device-side check failed
+};
+
+// allocation helpers (stream-ordered pool)
+int dalloc(void** p, size_t bytes, cudaStream_t s);
+void dfree(void* p, cudaStream_t s);
+
+int mat_alloc(spamm_ctx* ctx, int64_t n, int bs, int64_t cap, spamm_mat** out);
+int mat_compute_norms(spamm_ctx* ctx, spamm_mat* m);
+
+// scans (exclusive) of int32 counts into int64 offsets; total written to *d_total
+int scan_i32_to_i64(spamm_ctx* ctx, const int32_t* d_in, int64_t* d_out, int64_t count,
+                    unsigned long long* d_total);
+
+// CSE evaluation of one tau held in device memory (*d_tau_ptr); result into *d_err
+int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau_ptr,
+             double* d_err, const double* d_charge);
+// bisection for the tau index; fills DevScalars lo/hi/err_at_hi
+int cse_search(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double delta,
+               const double* d_charge, int* evals);
+
+// planning of the kept leaf products for C = A B (and the SP2 epilogue union)
+struct Plan {
+    int nb;
+    int64_t n_work;            // work items (CTAs of the leaf-product kernel)
+    int64_t n_out;             // output blocks
+    int64_t n_tasks;           // kept leaf products
+    int64_t n_cand;
+    int32_t* d_work_ij;        // [n_work] i*nb+j
+    int32_t* d_work_out;       // [n_work] output slot or -1
+    int64_t* d_work_off;       // [n_work+1] task offsets
+    int32_t* d_task_a;         // [n_tasks] slot of A_ik
+    int32_t* d_task_b;         // [n_tasks] slot of B_kj
+    int32_t* d_task_k;         // [n_tasks] k
+};
+// Builds the plan for the threshold at d_tau (device) and allocates the output
+// matrix (block map and slots filled; tiles written later by the leaf-product
+// kernel). X (may be null) adds its blocks as work items; mode_dbl adds them
+// as output blocks too (SP2 step 2X - X^2).
+int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau,
+                    const spamm_mat* X, int mode_dbl, Plan* plan, spamm_mat** C_out);
+void plan_free(Plan* plan, cudaStream_t s);
+
+// leaf products, FP64, with the fused epilogue
+struct Epilogue {
+    int mode;                  // 0: C = AB; 1: Xn = C (SP2 X^2); 2: Xn = 2X - C
+    const spamm_mat* X;        // SP2 input (modes 1 and 2), may be null in mode 0
+};
+int gemm_fp64(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const Plan& plan,
+              const Epilogue& ep, spamm_mat* C, double* d_part_fro2, double* d_part_trace,
+              double* d_part_idem2);
+
+// deterministic fixed-order sums of per-work-item partials into DevScalars
+int reduce_partials(spamm_ctx* ctx, const double* d_fro2, const double* d_trace,
+                    const double* d_idem2, int64_t count);
+
+// truncation on leaf blocks
+int truncate_blocks(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric,
+                    int64_t* removed, double* removed_sq);
+
+int mat_trace(spamm_ctx* ctx, const spamm_mat* X, double* trace);
+
+}  // namespace spamm

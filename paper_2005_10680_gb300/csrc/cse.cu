@@ -1,0 +1,236 @@
+// Algorithm 3 (Compute SpAMM Errors) on the GPU, and the tau search.
+//
+// The recursion of Algorithm 3 visits node triples (I, K, J) of the implicit
+// quadtree: A's node (I, K) times B's node (K, J). At the lowest level the
+// error of a triple is p = ||A_ik||_F ||B_kj||_F when 0 < p < tau (else 0);
+// one level up
+//     E(I,K,J) = sqrt( sum_{a,b in {0,1}} (E(2I+a, 2K, 2J+b) + E(2I+a, 2K+1, 2J+b))^2 ),
+// summed in the order (a,b) = (0,0), (0,1), (1,0), (1,1) as the recursion does,
+// and the bound for the whole product is E at the root.
+//
+// GPU form: the padded (i, k, j) leaf cube of side NB = 2^L is cut into 8^3
+// sub-cubes; one CTA of 512 threads owns a sub-cube, builds the leaf values
+// from the two dense norm maps (L2 resident), and folds three quadtree levels
+// in shared memory. The (NB/8)^3 results feed the same kernel again until one
+// value is left. One evaluation therefore costs NB^3 leaf visits, with no
+// storage for the triples.
+//
+// The tau search runs on the device: lo/hi bisection over the candidate index
+// (the bound is non-increasing in the index, because every operation in the
+// fold is monotone under round-to-nearest), so ceil(log2(N+1)) = 9 evaluations
+// replace the paper's 350-entry sweep and select the same candidate.
+#include "common.cuh"
+
+namespace spamm {
+
+constexpr int CUBE = 8;
+
+__device__ __forceinline__ int cube_coord(int t, int axis, int levels) {
+    // thread index bits: level m uses bits 3m (k), 3m+1 (i), 3m+2 (j)
+    int v = 0;
+    for (int m = 0; m < levels; ++m) v |= ((t >> (3 * m + axis)) & 1) << m;
+    return v;
+}
+
+// Fold `levels` quadtree levels of a c^3 cube held in sh[] (c = 2^levels) in place.
+__device__ __forceinline__ double fold_levels(double* sh, int levels) {
+    const int t = threadIdx.x;
+    int stride = 1;
+    for (int m = 0; m < levels; ++m) {
+        __syncthreads();
+        if ((t & (8 * stride - 1)) == 0) {
+            // children: offset b*stride with b = k + 2*i + 4*j
+            const double* x = sh + t;
+            double s00 = x[0 * stride] + x[1 * stride];   // i=0, j=0: k = 0, 1
+            double s01 = x[4 * stride] + x[5 * stride];   // i=0, j=1
+            double s10 = x[2 * stride] + x[3 * stride];   // i=1, j=0
+            double s11 = x[6 * stride] + x[7 * stride];   // i=1, j=1
+            double acc = 0.0;
+            acc += s00 * s00;
+            acc += s01 * s01;
+            acc += s10 * s10;
+            acc += s11 * s11;
+            sh[t] = sqrt(acc);
+        }
+        stride *= 8;
+    }
+    __syncthreads();
+    return sh[0];
+}
+
+// LEAF: values from norm maps; else: values from the previous level buffer.
+template <bool LEAF>
+__global__ void k_cse_cube(const double* __restrict__ nA, const double* __restrict__ nB, int nb,
+                           const double* __restrict__ in, int in_side,
+                           const double* __restrict__ d_tau, const double* __restrict__ d_charge,
+                           const int32_t* __restrict__ d_done, int levels,
+                           double* __restrict__ out) {
+    if (d_done && *d_done) return;
+    __shared__ double sh[CUBE * CUBE * CUBE];
+    const int c = 1 << levels;
+    const int t = threadIdx.x;
+    const int out_side = in_side / c;
+    const int bx = blockIdx.x;
+    const int J0 = (bx % out_side), K0 = (bx / out_side) % out_side, I0 = bx / (out_side * out_side);
+    const int i = I0 * c + cube_coord(t, 1, levels);
+    const int k = K0 * c + cube_coord(t, 0, levels);
+    const int j = J0 * c + cube_coord(t, 2, levels);
+    double v = 0.0;
+    if (LEAF) {
+        if (i < nb && k < nb && j < nb) {
+            const double tau = *d_tau;
+            const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
+            if (p != 0.0) {
+                if (p < tau) v = p;
+                else if (d_charge) v = 0.0;   // hook: rounding charge of kept products
+            }
+        }
+    } else {
+        v = in[((int64_t)i * in_side + k) * in_side + j];
+    }
+    sh[t] = v;
+    double r = fold_levels(sh, levels);
+    if (t == 0) out[((int64_t)I0 * out_side + K0) * out_side + J0] = r;
+}
+
+// E(tau) for the tau held at d_tau (device); result written to *d_err.
+int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau,
+                  const int32_t* d_done, double* d_err, const double* d_charge, double* buf0,
+                  double* buf1) {
+    cudaStream_t s = ctx->stream;
+    const int nb = A->nb;
+    int side = A->NB;
+    int L = 0;
+    while ((1 << L) < side) ++L;
+    if (L == 0) {
+        // a single leaf triple
+        k_cse_cube<true><<<1, 1, 0, s>>>(A->d_norm, B->d_norm, nb, nullptr, 1, d_tau, d_charge,
+                                         d_done, 0, d_err);
+        SP_CHECK_LAUNCH();
+        return SPAMM_OK;
+    }
+    int lv = L < 3 ? L : 3;
+    int out_side = side >> lv;
+    double* out = (out_side == 1) ? d_err : buf0;
+    k_cse_cube<true><<<out_side * out_side * out_side, 1 << (3 * lv), 0, s>>>(
+        A->d_norm, B->d_norm, nb, nullptr, side, d_tau, d_charge, d_done, lv, out);
+    SP_CHECK_LAUNCH();
+    L -= lv;
+    side = out_side;
+    double* in = buf0;
+    double* other = buf1;
+    while (L > 0) {
+        lv = L < 3 ? L : 3;
+        out_side = side >> lv;
+        out = (out_side == 1) ? d_err : other;
+        k_cse_cube<false><<<out_side * out_side * out_side, 1 << (3 * lv), 0, s>>>(
+            nullptr, nullptr, nb, in, side, d_tau, d_charge, d_done, lv, out);
+        SP_CHECK_LAUNCH();
+        L -= lv;
+        side = out_side;
+        double* tmp = in;
+        in = other;
+        other = tmp;
+    }
+    return SPAMM_OK;
+}
+
+static size_t level_buf_elems(const spamm_mat* A) {
+    int64_t s = A->NB >= 8 ? A->NB / 8 : 1;
+    return (size_t)(s * s * s);
+}
+
+int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau_ptr,
+             double* d_err, const double* d_charge) {
+    size_t e = level_buf_elems(A);
+    double *b0 = nullptr, *b1 = nullptr;
+    SP_TRY(dalloc((void**)&b0, sizeof(double) * e, ctx->stream));
+    SP_TRY(dalloc((void**)&b1, sizeof(double) * e, ctx->stream));
+    int st = cse_eval_impl(ctx, A, B, d_tau_ptr, nullptr, d_err, d_charge, b0, b1);
+    dfree(b0, ctx->stream);
+    dfree(b1, ctx->stream);
+    return st;
+}
+
+// --------------------------------------------------------------- bisection
+
+__global__ void k_bisect_init(DevScalars* sc, const double* __restrict__ tau, int N) {
+    sc->lo = 0;
+    sc->hi = N;
+    sc->done = 0;
+    sc->mid = N / 2;
+    sc->tau_mid = tau[N / 2];
+    sc->err_at_hi = 0.0;
+    sc->err_mid = 0.0;
+}
+
+__global__ void k_bisect_step(DevScalars* sc, const double* __restrict__ tau, double delta) {
+    if (sc->done) return;
+    if (sc->err_mid < delta) {
+        sc->hi = sc->mid;
+        sc->err_at_hi = sc->err_mid;
+    } else {
+        sc->lo = sc->mid + 1;
+    }
+    if (sc->lo >= sc->hi) {
+        sc->done = 1;
+    } else {
+        sc->mid = (sc->lo + sc->hi) / 2;
+        sc->tau_mid = tau[sc->mid];
+    }
+}
+
+int cse_search(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double delta,
+               const double* d_charge, int* evals) {
+    cudaStream_t s = ctx->stream;
+    DevScalars* sc = (DevScalars*)ctx->d_scalars;
+    size_t e = level_buf_elems(A);
+    double *b0 = nullptr, *b1 = nullptr;
+    SP_TRY(dalloc((void**)&b0, sizeof(double) * e, s));
+    SP_TRY(dalloc((void**)&b1, sizeof(double) * e, s));
+    const int N = SPAMM_N_TAU;
+    int steps = 0;
+    while ((1 << steps) < N + 1) ++steps;
+    k_bisect_init<<<1, 1, 0, s>>>(sc, ctx->d_tau, N);
+    int st = SPAMM_OK;
+    for (int it = 0; it < steps && st == SPAMM_OK; ++it) {
+        st = cse_eval_impl(ctx, A, B, &sc->tau_mid, &sc->done, &sc->err_mid, d_charge, b0, b1);
+        if (st == SPAMM_OK) {
+            k_bisect_step<<<1, 1, 0, s>>>(sc, ctx->d_tau, delta);
+            st = cudaGetLastError() == cudaSuccess ? SPAMM_OK : SPAMM_ECUDA;
+        }
+    }
+    dfree(b0, s);
+    dfree(b1, s);
+    if (evals) *evals = steps;
+    return st;
+}
+
+}  // namespace spamm
+
+using namespace spamm;
+
+extern "C" int spamm_cse(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B,
+                         const double* taus, int N, double* errors) {
+    if (!ctx || !A || !B || !taus || !errors || N < 0 || A->n != B->n || A->bs != B->bs) {
+        set_error("spamm_cse: bad argument");
+        return SPAMM_EINVAL;
+    }
+    SP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    double* d = nullptr;
+    SP_TRY(dalloc((void**)&d, sizeof(double) * 2 * (N > 0 ? N : 1), s));
+    SP_CUDA(cudaMemcpyAsync(d, taus, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+    size_t e = level_buf_elems(A);
+    double *b0 = nullptr, *b1 = nullptr;
+    SP_TRY(dalloc((void**)&b0, sizeof(double) * e, s));
+    SP_TRY(dalloc((void**)&b1, sizeof(double) * e, s));
+    for (int t = 0; t < N; ++t)
+        SP_TRY(cse_eval_impl(ctx, A, B, d + t, nullptr, d + N + t, nullptr, b0, b1));
+    SP_CUDA(cudaMemcpyAsync(errors, d + N, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    dfree(b0, s);
+    dfree(b1, s);
+    dfree(d, s);
+    return SPAMM_OK;
+}

@@ -1,0 +1,173 @@
+// Task planning for C = SpAMM(A, B, tau) (Algorithm 2, flattened).
+//
+// Because a quadtree node's norm is never smaller than a descendant's, the
+// lowest-level products that Algorithm 2 forms are exactly the leaf triples
+// (i, k, j) with A_ik and B_kj both stored and ||A_ik||_F ||B_kj||_F >= tau:
+// an internal node pruned by ||A|| ||B|| < tau only holds triples that the
+// leaf test prunes as well. So the plan keeps, for every output block (i, j),
+// the list of such k, in increasing k. Output block (i, j) exists when its
+// list is non-empty (fill-in from skipped products is never created) or, for
+// the SP2 step 2X - X^2, when X_ij is stored.
+//
+// One thread per output block walks k = 0..nb-1 over the two dense block maps;
+// three exclusive scans give work-item, output-slot and task offsets; a second
+// walk writes the (slot of A_ik, slot of B_kj) pairs.
+#include "common.cuh"
+
+namespace spamm {
+
+__global__ void k_plan_count(const int32_t* __restrict__ mapA, const double* __restrict__ nA,
+                             const int32_t* __restrict__ mapB, const double* __restrict__ nB,
+                             const int32_t* __restrict__ mapX, int nb, int mode_dbl,
+                             const double* __restrict__ d_tau, int32_t* __restrict__ cnt,
+                             int32_t* __restrict__ work_flag, int32_t* __restrict__ out_flag,
+                             unsigned long long* __restrict__ n_cand) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nb2 = (int64_t)nb * nb;
+    unsigned long long cand = 0;
+    if (b < nb2) {
+        const int i = (int)(b / nb), j = (int)(b % nb);
+        const double tau = *d_tau;
+        int kept = 0;
+        for (int k = 0; k < nb; ++k) {
+            const int32_t sa = mapA[(int64_t)i * nb + k];
+            const int32_t sb = mapB[(int64_t)k * nb + j];
+            if (sa < 0 || sb < 0) continue;
+            ++cand;
+            const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
+            if (!(p < tau)) ++kept;
+        }
+        const int hx = mapX ? (mapX[b] >= 0) : 0;
+        cnt[b] = kept;
+        const int of = kept > 0 || (mode_dbl && hx);
+        out_flag[b] = of;
+        work_flag[b] = of || hx;
+    }
+    // warp-aggregated candidate count
+    for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
+    if ((threadIdx.x & 31) == 0 && cand) atomicAdd(n_cand, cand);
+}
+
+__global__ void k_plan_fill(const int32_t* __restrict__ mapA, const double* __restrict__ nA,
+                            const int32_t* __restrict__ mapB, const double* __restrict__ nB,
+                            int nb, const double* __restrict__ d_tau,
+                            const int32_t* __restrict__ cnt, const int32_t* __restrict__ work_flag,
+                            const int32_t* __restrict__ out_flag,
+                            const int64_t* __restrict__ task_off, const int64_t* __restrict__ work_idx,
+                            const int64_t* __restrict__ out_idx, int32_t* __restrict__ work_ij,
+                            int32_t* __restrict__ work_out, int64_t* __restrict__ work_off,
+                            int32_t* __restrict__ task_a, int32_t* __restrict__ task_b,
+                            int32_t* __restrict__ mapC, int32_t* __restrict__ coordC) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nb2 = (int64_t)nb * nb;
+    if (b >= nb2 || !work_flag[b]) return;
+    const int i = (int)(b / nb), j = (int)(b % nb);
+    const int64_t w = work_idx[b];
+    const int64_t off = task_off[b];
+    const int32_t os = out_flag[b] ? (int32_t)out_idx[b] : -1;
+    work_ij[w] = (int32_t)b;
+    work_out[w] = os;
+    work_off[w] = off;
+    if (os >= 0) {
+        mapC[b] = os;
+        coordC[os] = (int32_t)b;
+    }
+    if (cnt[b] == 0) return;
+    const double tau = *d_tau;
+    int64_t t = off;
+    for (int k = 0; k < nb; ++k) {
+        const int32_t sa = mapA[(int64_t)i * nb + k];
+        const int32_t sb = mapB[(int64_t)k * nb + j];
+        if (sa < 0 || sb < 0) continue;
+        const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
+        if (!(p < tau)) {
+            task_a[t] = sa;
+            task_b[t] = sb;
+            ++t;
+        }
+    }
+}
+
+__global__ void k_plan_last_off(int64_t* work_off, int64_t n_work, const int64_t* task_off,
+                                int64_t nb2) {
+    work_off[n_work] = task_off[nb2];
+}
+
+void plan_free(Plan* p, cudaStream_t s) {
+    dfree(p->d_work_ij, s);
+    dfree(p->d_work_out, s);
+    dfree(p->d_work_off, s);
+    dfree(p->d_task_a, s);
+    dfree(p->d_task_b, s);
+    dfree(p->d_task_k, s);
+    *p = Plan();
+}
+
+// Builds the plan and the output matrix's block map (C must be allocated by the
+// caller afterwards with cap = plan->n_out; the map is written into *mapC_out
+// which the caller adopts).
+int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau,
+                    const spamm_mat* X, int mode_dbl, Plan* plan, spamm_mat** C_out) {
+    cudaStream_t s = ctx->stream;
+    DevScalars* sc = (DevScalars*)ctx->d_scalars;
+    const int nb = A->nb;
+    const int64_t nb2 = (int64_t)nb * nb;
+    *plan = Plan();
+    plan->nb = nb;
+    int32_t *cnt = nullptr, *wf = nullptr, *of = nullptr;
+    int64_t *toff = nullptr, *widx = nullptr, *oidx = nullptr;
+    SP_TRY(dalloc((void**)&cnt, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&wf, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&of, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&toff, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&widx, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&oidx, sizeof(int64_t) * (nb2 + 1), s));
+    SP_CUDA(cudaMemsetAsync(&sc->n_cand, 0, sizeof(unsigned long long), s));
+    const int T = 256;
+    const unsigned G = (unsigned)((nb2 + T - 1) / T);
+    k_plan_count<<<G, T, 0, s>>>(A->d_map, A->d_norm, B->d_map, B->d_norm, X ? X->d_map : nullptr,
+                                 nb, mode_dbl, d_tau, cnt, wf, of, &sc->n_cand);
+    SP_CHECK_LAUNCH();
+    SP_TRY(scan_i32_to_i64(ctx, cnt, toff, nb2, &sc->n_tasks));
+    unsigned long long* d_nwork = nullptr;
+    SP_TRY(dalloc((void**)&d_nwork, sizeof(unsigned long long), s));
+    SP_TRY(scan_i32_to_i64(ctx, wf, widx, nb2, d_nwork));
+    SP_TRY(scan_i32_to_i64(ctx, of, oidx, nb2, &sc->n_out));
+    unsigned long long h[3];
+    SP_CUDA(cudaMemcpyAsync(&h[0], &sc->n_tasks, 8, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaMemcpyAsync(&h[1], d_nwork, 8, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaMemcpyAsync(&h[2], &sc->n_out, 8, cudaMemcpyDeviceToHost, s));
+    unsigned long long hc = 0;
+    SP_CUDA(cudaMemcpyAsync(&hc, &sc->n_cand, 8, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    plan->n_tasks = (int64_t)h[0];
+    plan->n_work = (int64_t)h[1];
+    plan->n_out = (int64_t)h[2];
+    plan->n_cand = (int64_t)hc;
+    spamm_mat* C = nullptr;
+    SP_TRY(mat_alloc(ctx, A->n, A->bs, plan->n_out, &C));
+    C->nslots = plan->n_out;
+    C->nnzb = plan->n_out;
+    SP_TRY(dalloc((void**)&plan->d_work_ij, sizeof(int32_t) * (plan->n_work + 1), s));
+    SP_TRY(dalloc((void**)&plan->d_work_out, sizeof(int32_t) * (plan->n_work + 1), s));
+    SP_TRY(dalloc((void**)&plan->d_work_off, sizeof(int64_t) * (plan->n_work + 1), s));
+    SP_TRY(dalloc((void**)&plan->d_task_a, sizeof(int32_t) * (plan->n_tasks + 1), s));
+    SP_TRY(dalloc((void**)&plan->d_task_b, sizeof(int32_t) * (plan->n_tasks + 1), s));
+    k_plan_fill<<<G, T, 0, s>>>(A->d_map, A->d_norm, B->d_map, B->d_norm, nb, d_tau, cnt, wf, of,
+                                toff, widx, oidx, plan->d_work_ij, plan->d_work_out,
+                                plan->d_work_off, plan->d_task_a, plan->d_task_b, C->d_map,
+                                C->d_coord);
+    k_plan_last_off<<<1, 1, 0, s>>>(plan->d_work_off, plan->n_work, toff, nb2);
+    SP_CHECK_LAUNCH();
+    dfree(cnt, s);
+    dfree(wf, s);
+    dfree(of, s);
+    dfree(toff, s);
+    dfree(widx, s);
+    dfree(oidx, s);
+    dfree(d_nwork, s);
+    *C_out = C;
+    return SPAMM_OK;
+}
+
+}  // namespace spamm
