@@ -63,9 +63,16 @@ typedef struct {
     int32_t tau_index;     /* 0-based index into the candidate table, -1 if none */
     int32_t cse_evals;     /* Algorithm 3 evaluations run by the tau search */
     double bound;          /* certified ||SpAMM(A,B,tau) - AB||_F bound (Alg. 3), incl. bound_round */
-    double bound_round;    /* part of bound charged for mixed-precision leaf products */
+    double bound_round;    /* mixed form: Algorithm 3 bound of the slicing charges alone
+                              (every product kept); 0 for float64 leaf products */
+    int32_t lmax;          /* mixed form: highest slice level p + q formed; 0 = float64 */
+    int32_t reserved;
     int64_t candidates;    /* leaf triples (i,k,j) with A_ik and B_kj both present */
-    int64_t kept;          /* leaf products formed (p >= tau) */
+    int64_t kept;          /* kept leaf triples of the product (p >= tau) */
+    int64_t formed;        /* leaf products multiplied: == kept, except SP2 steps, which form
+                              blocks i <= j only and mirror them (X symmetric) */
+    double pipe_flops;     /* arithmetic issued by the leaf-product kernel: 2 bs^3 per formed
+                              product (FP64), or 2*128*64*64 per (p,q) slice pair (mixed) */
     int64_t nnzb_out;      /* leaf blocks in the result */
     double fro_out;        /* ||result||_F */
     double trace_out;      /* trace of the result */
@@ -78,11 +85,21 @@ typedef struct {
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
-   owned by the caller, or NULL to let the context create (and own) one. */
+   owned by the caller, or NULL to let the context create (and own) one.
+   spamm_destroy may be called while matrices of the context are alive: the
+   context (and its stream) is released when the last of them is freed. */
 int spamm_create(spamm_ctx** ctx, int device, void* cuda_stream);
 void spamm_destroy(spamm_ctx* ctx);
 const char* spamm_strerror(int status);
 const char* spamm_last_error(void);
+
+/* Number of CUDA kernels this context has launched so far (a profiling counter:
+   every kernel launch site of the library increments it on the host). */
+int64_t spamm_ctx_launches(const spamm_ctx* ctx);
+
+/* 1 when leaf products in precision `prec` with leaf size `bs` are built for
+   the context's device, else 0. */
+int spamm_prec_supported(const spamm_ctx* ctx, spamm_prec prec, int bs);
 
 /* --------------------------------------------------------------- matrices */
 
@@ -160,7 +177,9 @@ typedef struct {
     double idem;             /* last ||X^2 - X||_F estimate (+ its multiply bound) */
     double trace;            /* trace of the returned D */
     double lmin, lmax;       /* spectral bounds used for X_0 */
-    int64_t kept_total;      /* leaf products formed over all steps */
+    int64_t kept_total;      /* kept leaf triples over all steps */
+    int64_t formed_total;    /* leaf products multiplied over all steps */
+    double pipe_flops_total; /* leaf-product kernel arithmetic over all steps */
     int64_t cand_total;      /* leaf triples considered over all steps */
     double ms_total;         /* wall time of the purification (CUDA events) */
     double ms_phase[8];      /* phase totals, indexed by SPAMM_T_* */

@@ -23,8 +23,11 @@ class SpammError(RuntimeError):
 class Report(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tau_index", ctypes.c_int32),
                 ("cse_evals", ctypes.c_int32), ("bound", ctypes.c_double),
-                ("bound_round", ctypes.c_double), ("candidates", ctypes.c_int64),
-                ("kept", ctypes.c_int64), ("nnzb_out", ctypes.c_int64),
+                ("bound_round", ctypes.c_double), ("lmax", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("candidates", ctypes.c_int64),
+                ("kept", ctypes.c_int64), ("formed", ctypes.c_int64),
+                ("pipe_flops", ctypes.c_double),
+                ("nnzb_out", ctypes.c_int64),
                 ("fro_out", ctypes.c_double), ("trace_out", ctypes.c_double),
                 ("idem", ctypes.c_double), ("removed_sq", ctypes.c_double),
                 ("removed_blocks", ctypes.c_int64), ("ms", ctypes.c_float * 8)]
@@ -50,7 +53,9 @@ class PurifyReport(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
                 ("idem", ctypes.c_double), ("trace", ctypes.c_double),
                 ("lmin", ctypes.c_double), ("lmax", ctypes.c_double),
-                ("kept_total", ctypes.c_int64), ("cand_total", ctypes.c_int64),
+                ("kept_total", ctypes.c_int64), ("formed_total", ctypes.c_int64),
+                ("pipe_flops_total", ctypes.c_double),
+                ("cand_total", ctypes.c_int64),
                 ("ms_total", ctypes.c_double), ("ms_phase", ctypes.c_double * 8),
                 ("step_delta", _PD), ("step_tau", _PD), ("step_trace", _PD),
                 ("step_idem", _PD), ("step_branch", _PI32), ("step_nnzb", _PI64)]
@@ -82,6 +87,8 @@ def load_library(build_if_stale: bool = True):
         "spamm_destroy": ([vp], None),
         "spamm_strerror": ([i32], ctypes.c_char_p),
         "spamm_last_error": ([], ctypes.c_char_p),
+        "spamm_ctx_launches": ([vp], i64),
+        "spamm_prec_supported": ([vp, i32, i32], i32),
         "spamm_mat_from_dense": ([vp, vp, i64, i64, i32, d, i32, P(vp)], i32),
         "spamm_mat_to_dense": ([vp, vp, vp, i64, i32], i32),
         "spamm_mat_info": ([vp, P(i64), P(i32), P(i64)], i32),
@@ -178,6 +185,16 @@ class Matrix:
                "spamm_mat_to_dense")
         return out
 
+    def to_host(self, out):
+        """Write densely into a host buffer (numpy array or CPU torch tensor,
+        ideally pinned), n x n float64 C-contiguous."""
+        n = self.n
+        ptr = out.data_ptr() if _is_torch(out) else out.ctypes.data
+        assert tuple(out.shape) == (n, n)
+        _check(_lib.spamm_mat_to_dense(self.ctx.handle, self.handle, ptr, n, 0),
+               "spamm_mat_to_dense")
+        return out
+
     def block_norms(self) -> np.ndarray:
         nb = self.nb
         out = np.empty((nb, nb))
@@ -212,6 +229,13 @@ class Context:
         if h is not None and h.value and _lib is not None:
             _lib.spamm_destroy(h)
             self.handle = None
+
+    def supports(self, prec="mixed", bs: int = 64) -> bool:
+        return bool(_lib.spamm_prec_supported(self.handle, _PREC[prec], bs))
+
+    def launches(self) -> int:
+        """Kernels launched through this context so far."""
+        return int(_lib.spamm_ctx_launches(self.handle))
 
     def sync_torch(self):
         """Order the library's stream after torch work on the current stream."""
@@ -300,6 +324,7 @@ class Context:
         it = rep.iters
         r = {"iters": it, "converged": bool(rep.converged), "idem": rep.idem, "trace": rep.trace,
              "lmin": rep.lmin, "lmax": rep.lmax, "kept_total": rep.kept_total,
+             "formed_total": rep.formed_total, "pipe_flops_total": rep.pipe_flops_total,
              "cand_total": rep.cand_total, "ms_total": rep.ms_total,
              "ms_phase": list(rep.ms_phase), "status": st,
              "deltas": logs["delta"][:it].tolist(), "taus": logs["tau"][:it].tolist(),

@@ -6,12 +6,6 @@
 
 #include "common.cuh"
 
-namespace spamm {
-int mixed_available();
-int gemm_mixed(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const Plan& plan,
-               const Epilogue& ep, spamm_mat* C, double* d_part_fro2, double* d_part_trace,
-               double* d_part_idem2);
-}
 
 using namespace spamm;
 
@@ -60,39 +54,109 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     spamm_report r;
     memset(&r, 0, sizeof r);
     cudaEventRecord(ctx->ev[EV_T0], s);
+    // SP2 steps multiply a symmetric X by itself: use a bitwise-symmetric norm map
+    // so that the kept set of (j, i) is exactly the transpose of that of (i, j),
+    // and form only the blocks i <= j.
+    const int sym = mode != 0;
+    const double* nA = A->d_norm;
+    const double* nB = B->d_norm;
+    double* nsym = nullptr;
+    if (sym) {
+        SP_TRY(dalloc((void**)&nsym, sizeof(double) * (size_t)A->nb * A->nb, s));
+        SP_TRY(sym_norms(ctx, A->d_norm, A->nb, nsym));
+        nA = nB = nsym;
+    }
     int evals = 0;
-    if (search) {
-        SP_TRY(cse_search(ctx, A, B, delta, nullptr, &evals));
-        k_select_tau<<<1, 1, 0, s>>>(sc, ctx->d_tau, SPAMM_N_TAU);
-    } else {
-        k_set_tau<<<1, 1, 0, s>>>(sc, tau);
-        SP_TRY(cse_eval(ctx, A, B, &sc->tau_sel, &sc->err_at_hi, nullptr));
-        evals = 1;
-    }
-    SP_CHECK_LAUNCH();
-    cudaEventRecord(ctx->ev[EV_CSE1], s);
-    Plan plan;
+    int64_t n_cand = 0, n_tasks = 0, n_kept = 0;
     spamm_mat* C = nullptr;
-    SP_TRY(plan_build_impl(ctx, A, B, &sc->tau_sel, mode ? A : nullptr, mode == 2, &plan, &C));
-    cudaEventRecord(ctx->ev[EV_PLAN1], s);
+    int st = SPAMM_OK;
+    double err_charge = 0.0;
+    int lmax_used = 0;
+    MixedPrep mp;
+    bool use_mixed = prec == SPAMM_MIXED;
+    if (use_mixed) {
+        st = mixed_prepare(ctx, A, B, sym, &mp);
+        if (st != SPAMM_OK) {
+            dfree(nsym, s);
+            return st;
+        }
+        cudaEventRecord(ctx->ev[EV_CSE0], s);
+        // fewest levels whose certified charge (everything kept, tau = 0) stays within
+        // half of delta; with a given tau all 9 levels are formed
+        lmax_used = 0;
+        const int first = search ? 4 : 9;
+        for (int L = first; L <= 9 && st == SPAMM_OK; ++L) {
+            ChargeData ch = mixed_charge(A, B, nA, nB, mp, L);
+            ++ctx->launches;
+            k_set_tau<<<1, 1, 0, s>>>(sc, 0.0);
+            st = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_charge, ch);
+            if (st != SPAMM_OK) break;
+            double ec = 0.0;
+            cudaMemcpyAsync(&ec, &sc->err_charge, 8, cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
+            ++evals;
+            if (!search || ec <= 0.5 * delta) {
+                lmax_used = L;
+                err_charge = ec;
+                break;
+            }
+        }
+        if (st == SPAMM_OK && lmax_used == 0) {
+            // the slices cannot certify delta: fall back to float64 leaf products
+            mixed_release(ctx, &mp);
+            use_mixed = false;
+        }
+    }
+    if (st == SPAMM_OK) {
+        ChargeData ch = use_mixed ? mixed_charge(A, B, nA, nB, mp, lmax_used) : ChargeData();
+        int ev2 = 0;
+        if (search) {
+            st = cse_search(ctx, A, nA, nB, delta, ch, &ev2);
+            ++ctx->launches;
+            k_select_tau<<<1, 1, 0, s>>>(sc, ctx->d_tau, SPAMM_N_TAU);
+        } else {
+            ++ctx->launches;
+            k_set_tau<<<1, 1, 0, s>>>(sc, tau);
+            st = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_at_hi, ch);
+            ev2 = 1;
+        }
+        evals += ev2;
+    }
+    cudaEventRecord(ctx->ev[EV_CSE1], s);
     double* parts = nullptr;
-    int64_t nw = plan.n_work > 0 ? plan.n_work : 1;
-    int st = dalloc((void**)&parts, sizeof(double) * 3 * nw, s);
-    if (st == SPAMM_OK) {
-        Epilogue ep{mode, mode ? A : nullptr};
-        if (prec == SPAMM_FP64)
+    if (st == SPAMM_OK && use_mixed) {
+        int64_t npairs = 0;
+        st = mixed_plan_and_gemm(ctx, A, B, nA, nB, &sc->tau_sel, mp, lmax_used, mode, sym, &C,
+                                 &n_cand, &n_kept, &n_tasks, &npairs);
+        cudaEventRecord(ctx->ev[EV_PLAN1], s);
+        cudaEventRecord(ctx->ev[EV_GEMM1], s);
+        mixed_release(ctx, &mp);
+    } else if (st == SPAMM_OK) {
+        Plan plan;
+        st = plan_build_impl(ctx, A, B, nA, nB, &sc->tau_sel, mode ? A : nullptr, mode == 2, sym,
+                             &plan, &C);
+        cudaEventRecord(ctx->ev[EV_PLAN1], s);
+        int64_t nw = plan.n_work > 0 ? plan.n_work : 1;
+        if (st == SPAMM_OK) st = dalloc((void**)&parts, sizeof(double) * 3 * nw, s);
+        if (st == SPAMM_OK) {
+            Epilogue ep{mode, mode ? A : nullptr};
             st = gemm_fp64(ctx, A, B, plan, ep, C, parts, parts + nw, parts + 2 * nw);
-        else
-            st = gemm_mixed(ctx, A, B, plan, ep, C, parts, parts + nw, parts + 2 * nw);
+        }
+        cudaEventRecord(ctx->ev[EV_GEMM1], s);
+        if (st == SPAMM_OK) {
+            if (plan.n_work > 0)
+                st = reduce_partials(ctx, parts, parts + nw, parts + 2 * nw, plan.n_work);
+            else
+                st = cudaMemsetAsync(&sc->fro2, 0, 3 * sizeof(double), s) == cudaSuccess
+                         ? SPAMM_OK
+                         : SPAMM_ECUDA;
+        }
+        n_cand = plan.n_cand;
+        n_tasks = plan.n_tasks;
+        n_kept = plan.n_kept_full;
+        plan_free(&plan, s);
     }
-    cudaEventRecord(ctx->ev[EV_GEMM1], s);
-    if (st == SPAMM_OK) {
-        if (plan.n_work > 0)
-            st = reduce_partials(ctx, parts, parts + nw, parts + 2 * nw, plan.n_work);
-        else
-            st = cudaMemsetAsync(&sc->fro2, 0, 3 * sizeof(double), s) == cudaSuccess ? SPAMM_OK
-                                                                                     : SPAMM_ECUDA;
-    }
+    dfree(nsym, s);
     cudaEventRecord(ctx->ev[EV_END], s);
     DevScalars h;
     if (st == SPAMM_OK) {
@@ -100,9 +164,11 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "report copy", __FILE__, __LINE__);
     }
-    const int64_t n_cand = plan.n_cand, n_tasks = plan.n_tasks;
     dfree(parts, s);
-    plan_free(&plan, s);
+    if (st == SPAMM_OK && h.status != 0) {
+        set_error("mixed leaf-product kernel: a bounded wait gave up (code %d)", h.status);
+        st = SPAMM_ETIMEOUT;
+    }
     if (st != SPAMM_OK) {
         spamm_mat_free(C);
         return st;
@@ -111,14 +177,19 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     r.tau_index = search ? (h.hi < SPAMM_N_TAU ? h.hi : -1) : -1;
     r.cse_evals = evals;
     r.bound = (search && h.hi >= SPAMM_N_TAU) ? 0.0 : h.err_at_hi;
-    r.bound_round = 0.0;
+    r.bound_round = use_mixed ? err_charge : 0.0;
+    r.lmax = use_mixed ? lmax_used : 0;
     r.candidates = n_cand;
-    r.kept = n_tasks;
+    r.kept = n_kept;
+    r.formed = use_mixed ? (int64_t)h.mx_formed : n_tasks;
+    r.pipe_flops = use_mixed ? (double)h.mx_pairs * 2.0 * 128 * 64 * 64
+                             : 2.0 * A->bs * A->bs * A->bs * (double)n_tasks;
     r.nnzb_out = C->nnzb;
     r.fro_out = std::sqrt(h.fro2);
     r.trace_out = h.trace;
     r.idem = std::sqrt(h.idem2);
-    r.ms[SPAMM_T_CSE] = ev_ms(ctx, EV_T0, EV_CSE1);
+    r.ms[SPAMM_T_SPLIT] = use_mixed ? ev_ms(ctx, EV_T0, EV_CSE0) : 0.f;
+    r.ms[SPAMM_T_CSE] = ev_ms(ctx, use_mixed ? EV_CSE0 : EV_T0, EV_CSE1);
     r.ms[SPAMM_T_PLAN] = ev_ms(ctx, EV_CSE1, EV_PLAN1);
     r.ms[SPAMM_T_GEMM] = ev_ms(ctx, EV_PLAN1, EV_GEMM1);
     r.ms[SPAMM_T_TOTAL] = ev_ms(ctx, EV_T0, EV_END);
@@ -216,6 +287,7 @@ int make_x0(spamm_ctx* ctx, const spamm_mat* F, double lmin, double lmax, spamm_
     SP_TRY(dalloc((void**)&flag, sizeof(int32_t) * nb2, s));
     SP_TRY(dalloc((void**)&slot, sizeof(int64_t) * (nb2 + 1), s));
     SP_TRY(dalloc((void**)&tot, 8, s));
+    ++ctx->launches;
     k_x0_flags<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(F->d_map, nb, flag);
     SP_TRY(scan_i32_to_i64(ctx, flag, slot, nb2, tot));
     unsigned long long cnt = 0;
@@ -224,6 +296,7 @@ int make_x0(spamm_ctx* ctx, const spamm_mat* F, double lmin, double lmax, spamm_
     spamm_mat* X = nullptr;
     SP_TRY(mat_alloc(ctx, F->n, F->bs, (int64_t)cnt, &X));
     X->nslots = X->nnzb = (int64_t)cnt;
+    ++ctx->launches;
     k_x0_fill<<<(unsigned)nb2, 256, 0, s>>>(F->d_tiles, F->d_map, flag, slot, nb, F->bs, F->n,
                                             lmax, lmax - lmin, X->d_map, X->d_coord, X->d_tiles);
     SP_CHECK_LAUNCH();
@@ -302,8 +375,23 @@ extern "C" int spamm_create(spamm_ctx** out, int device, void* cuda_stream) {
     return SPAMM_OK;
 }
 
-extern "C" void spamm_destroy(spamm_ctx* c) {
-    if (!c) return;
+extern "C" int64_t spamm_ctx_launches(const spamm_ctx* c) {
+    return c ? (int64_t)c->launches : 0;
+}
+
+extern "C" int spamm_prec_supported(const spamm_ctx* c, spamm_prec prec, int bs) {
+    if (!c || !(bs == 32 || bs == 64 || bs == 128)) return 0;
+    if (prec == SPAMM_FP64) return 1;
+    if (prec == SPAMM_MIXED) return mixed_available() && bs == 64;
+    return 0;
+}
+
+namespace spamm {
+// A context outlives the matrices allocated through it: their storage is
+// ordered on its stream, so the stream is destroyed only when the last of
+// them is freed.
+void ctx_release(spamm_ctx* c) {
+    if (!c || !c->closed || c->refs > 0) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 12; ++i)
@@ -312,6 +400,13 @@ extern "C" void spamm_destroy(spamm_ctx* c) {
     cudaFree(c->d_scalars);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
+}
+}  // namespace spamm
+
+extern "C" void spamm_destroy(spamm_ctx* c) {
+    if (!c) return;
+    c->closed = 1;
+    ctx_release(c);
 }
 
 extern "C" int spamm_multiply(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double delta,
@@ -390,7 +485,8 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
     else memset(&R, 0, sizeof R);
     R.iters = 0;
     R.converged = 0;
-    R.kept_total = R.cand_total = 0;
+    R.kept_total = R.cand_total = R.formed_total = 0;
+    R.pipe_flops_total = 0.0;
     for (int i = 0; i < 8; ++i) R.ms_phase[i] = 0.0;
     cudaEvent_t e0, e1;
     SP_CUDA(cudaEventCreate(&e0));
@@ -402,8 +498,10 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
         double *part = nullptr, *mm = nullptr;
         SP_TRY(dalloc((void**)&part, sizeof(double) * 2 * F->nb, s));
         SP_TRY(dalloc((void**)&mm, sizeof(double) * 2, s));
+        ++ctx->launches;
         k_gershgorin<<<F->nb, F->bs, 0, s>>>(F->d_tiles, F->d_map, F->nb, F->bs, F->n, part,
                                              part + F->nb);
+        ++ctx->launches;
         k_minmax<<<1, 1, 0, s>>>(part, part + F->nb, F->nb, mm);
         SP_CHECK_LAUNCH();
         double h[2];
@@ -459,6 +557,8 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
                                 0.0, opts->prec, &Xn, &mr);
         if (st != SPAMM_OK) break;
         R.kept_total += mr.kept;
+        R.formed_total += mr.formed;
+        R.pipe_flops_total += mr.pipe_flops;
         R.cand_total += mr.candidates;
         for (int q = 0; q < 8; ++q) R.ms_phase[q] += mr.ms[q];
         idem = mr.idem + mr.bound;

@@ -43,9 +43,13 @@ struct spamm_ctx {
     void* d_scalars;             // see struct DevScalars
     void* h_scalars;             // pinned host mirror
     cudaEvent_t ev[12];
+    unsigned long long launches;  // kernels launched through this context
+    int refs;                     // matrices allocated through this context and not yet freed
+    int closed;                   // spamm_destroy was called; freed when refs reaches 0
 };
 
 struct spamm_mat {
+    spamm_ctx* ctx;              // owning context (kept alive until this matrix is freed)
     int device;
     cudaStream_t stream;         // stream the storage is ordered on
     int64_t n;
@@ -77,8 +81,12 @@ struct DevScalars {
     unsigned long long n_out;       // output blocks
     unsigned long long n_tasks;     // kept leaf products
     unsigned long long n_cand;      // candidate triples
-    // reductions
+    unsigned long long n_kept_full; // kept triples of the full product (must follow n_cand)
+    // reductions (fro2, trace, idem2 must stay adjacent)
     double fro2, trace, idem2, bound_round2;
+    double err_charge;               // Algorithm 3 bound with tau = 0 (mixed charges only)
+    unsigned long long mx_formed;    // mixed: leaf products formed (block halves of pair tasks)
+    unsigned long long mx_pairs;     // mixed: (p, q) slice pairs issued (4 MMAs of 128x64x16 each)
     // truncation
     unsigned long long trunc_removed;
     double trunc_removed_sq;
@@ -93,18 +101,72 @@ int dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
 
 int mat_alloc(spamm_ctx* ctx, int64_t n, int bs, int64_t cap, spamm_mat** out);
+void ctx_release(spamm_ctx* ctx);   // frees a closed context once no matrix refers to it
 int mat_compute_norms(spamm_ctx* ctx, spamm_mat* m);
 
 // scans (exclusive) of int32 counts into int64 offsets; total written to *d_total
 int scan_i32_to_i64(spamm_ctx* ctx, const int32_t* d_in, int64_t* d_out, int64_t count,
                     unsigned long long* d_total);
 
+// Charge of the mixed-precision leaf products (see mixed.cu): per stored block,
+// slice norms sn[p] = ||X_p||_F and tail norms tn[p] = ||X - sum_{q<=p} X_q||_F,
+// p = 1..8. A product formed from the level pairs p + q <= lmax has error at most
+//   sum_{p=1}^{lmax-1} snA[p] tnB[lmax-p] + tnA[lmax-1] ||B_kj||_F.
+// lmax = 0 means "no charge" (float64 leaf products).
+struct ChargeData {
+    int nb = 0;
+    int lmax = 0;
+    int bt_from_a = 0;             // B operand of (i,k,j) is A's block (j,k) (symmetric X)
+    const int32_t* mapA = nullptr;
+    const int32_t* mapB = nullptr;
+    const double* nA = nullptr;
+    const double* nB = nullptr;
+    const double* snA = nullptr;
+    const double* tnA = nullptr;
+    const double* snB = nullptr;
+    const double* tnB = nullptr;
+};
+
+__device__ __forceinline__ double charge(const ChargeData& ch, int32_t sa, int32_t sb,
+                                         double norm_b) {
+    const int L = ch.lmax;
+    const double* snA = ch.snA + (int64_t)sa * 8;
+    const double* tnA = ch.tnA + (int64_t)sa * 8;
+    const double* tnB = ch.tnB + (int64_t)sb * 8;
+    double c = tnA[L - 2] * norm_b;
+    for (int p = 1; p <= L - 1; ++p) c = fma(snA[p - 1], tnB[L - p - 1], c);
+    return c;
+}
+
+// slot of the B operand's slices for triple (i, k, j)
+__device__ __forceinline__ int32_t charge_bslot(const ChargeData& ch, int k, int j) {
+    return ch.bt_from_a ? ch.mapA[(int64_t)j * ch.nb + k] : ch.mapB[(int64_t)k * ch.nb + j];
+}
+
+struct MixedPrep {
+    void* sa = nullptr;
+    void* sb = nullptr;
+    int sym = 0;
+};
+int mixed_available();
+int mixed_prepare(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, int sym, MixedPrep* mp);
+void mixed_release(spamm_ctx* ctx, MixedPrep* mp);
+ChargeData mixed_charge(const spamm_mat* A, const spamm_mat* B, const double* nA,
+                        const double* nB, const MixedPrep& mp, int lmax);
+int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
+                        const double* nB, const double* d_tau, const MixedPrep& mp, int lmax,
+                        int mode, int sym, spamm_mat** C_out, int64_t* n_cand, int64_t* n_kept,
+                        int64_t* n_formed, int64_t* n_pairs);
+
 // CSE evaluation of one tau held in device memory (*d_tau_ptr); result into *d_err
-int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau_ptr,
-             double* d_err, const double* d_charge);
+// nA, nB: the leaf norm maps to use (the matrices' own, or a symmetrised copy)
+int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
+             const double* d_tau_ptr, double* d_err, const ChargeData& ch);
 // bisection for the tau index; fills DevScalars lo/hi/err_at_hi
-int cse_search(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double delta,
-               const double* d_charge, int* evals);
+int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
+               double delta, const ChargeData& ch, int* evals);
+// out[i,j] = in[min(i,j), max(i,j)]: a bitwise-symmetric copy of a norm map
+int sym_norms(spamm_ctx* ctx, const double* in, int nb, double* out);
 
 // planning of the kept leaf products for C = A B (and the SP2 epilogue union)
 struct Plan {
@@ -113,8 +175,11 @@ struct Plan {
     int64_t n_out;             // output blocks
     int64_t n_tasks;           // kept leaf products
     int64_t n_cand;
+    int64_t n_kept_full;       // kept triples of the full product (n_tasks counts the formed ones)
     int32_t* d_work_ij;        // [n_work] i*nb+j
     int32_t* d_work_out;       // [n_work] output slot or -1
+    int32_t* d_work_out_t;     // [n_work] slot of the mirror block (symmetric mode) or -1
+    int sym;                   // symmetric mode: work items are blocks i <= j
     int64_t* d_work_off;       // [n_work+1] task offsets
     int32_t* d_task_a;         // [n_tasks] slot of A_ik
     int32_t* d_task_b;         // [n_tasks] slot of B_kj
@@ -124,9 +189,18 @@ struct Plan {
 // matrix (block map and slots filled; tiles written later by the leaf-product
 // kernel). X (may be null) adds its blocks as work items; mode_dbl adds them
 // as output blocks too (SP2 step 2X - X^2).
-int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau,
-                    const spamm_mat* X, int mode_dbl, Plan* plan, spamm_mat** C_out);
+int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
+                    const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
+                    int sym, Plan* plan, spamm_mat** C_out);
 void plan_free(Plan* plan, cudaStream_t s);
+// block-level keep counts (cnt), work flags (wf) and output flags (of) over the nb x nb
+// blocks; ch->lmax > 0 applies the mixed keep rule (charge below the norm product)
+int plan_count_blocks(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
+                      const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
+                      int sym, const ChargeData* ch, int32_t* cnt, int32_t* wf, int32_t* of);
+// mapC[b] = out slot for every flagged block, and the slot -> block coordinates
+int plan_write_out_map(spamm_ctx* ctx, const int32_t* of, const int64_t* oidx, int nb,
+                       spamm_mat* C);
 
 // leaf products, FP64, with the fused epilogue
 struct Epilogue {

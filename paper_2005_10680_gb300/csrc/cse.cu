@@ -62,7 +62,7 @@ __device__ __forceinline__ double fold_levels(double* sh, int levels) {
 template <bool LEAF>
 __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restrict__ nB, int nb,
                            const double* __restrict__ in, int in_side,
-                           const double* __restrict__ d_tau, const double* __restrict__ d_charge,
+                           const double* __restrict__ d_tau, ChargeData ch,
                            const int32_t* __restrict__ d_done, int levels,
                            double* __restrict__ out) {
     if (d_done && *d_done) return;
@@ -81,8 +81,15 @@ __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restri
             const double tau = *d_tau;
             const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
             if (p != 0.0) {
-                if (p < tau) v = p;
-                else if (d_charge) v = 0.0;   // hook: rounding charge of kept products
+                if (p < tau) {
+                    v = p;
+                } else if (ch.lmax > 0) {
+                    // kept: the mixed-precision product's error, or the whole product
+                    // when the charge is not below it (then it is not formed)
+                    const int32_t sa = ch.mapA[(int64_t)i * nb + k];
+                    const int32_t sb = charge_bslot(ch, k, j);
+                    v = fmin(p, charge(ch, sa, sb, nB[(int64_t)k * nb + j]));
+                }
             }
         }
     } else {
@@ -94,9 +101,9 @@ __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restri
 }
 
 // E(tau) for the tau held at d_tau (device); result written to *d_err.
-int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau,
-                  const int32_t* d_done, double* d_err, const double* d_charge, double* buf0,
-                  double* buf1) {
+int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
+                  const double* d_tau, const int32_t* d_done, double* d_err,
+                  const ChargeData& d_charge, double* buf0, double* buf1) {
     cudaStream_t s = ctx->stream;
     const int nb = A->nb;
     int side = A->NB;
@@ -104,7 +111,8 @@ int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const 
     while ((1 << L) < side) ++L;
     if (L == 0) {
         // a single leaf triple
-        k_cse_cube<true><<<1, 1, 0, s>>>(A->d_norm, B->d_norm, nb, nullptr, 1, d_tau, d_charge,
+        ++ctx->launches;
+        k_cse_cube<true><<<1, 1, 0, s>>>(nA, nB, nb, nullptr, 1, d_tau, d_charge,
                                          d_done, 0, d_err);
         SP_CHECK_LAUNCH();
         return SPAMM_OK;
@@ -112,8 +120,9 @@ int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const 
     int lv = L < 3 ? L : 3;
     int out_side = side >> lv;
     double* out = (out_side == 1) ? d_err : buf0;
+    ++ctx->launches;
     k_cse_cube<true><<<out_side * out_side * out_side, 1 << (3 * lv), 0, s>>>(
-        A->d_norm, B->d_norm, nb, nullptr, side, d_tau, d_charge, d_done, lv, out);
+        nA, nB, nb, nullptr, side, d_tau, d_charge, d_done, lv, out);
     SP_CHECK_LAUNCH();
     L -= lv;
     side = out_side;
@@ -123,6 +132,7 @@ int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const 
         lv = L < 3 ? L : 3;
         out_side = side >> lv;
         out = (out_side == 1) ? d_err : other;
+        ++ctx->launches;
         k_cse_cube<false><<<out_side * out_side * out_side, 1 << (3 * lv), 0, s>>>(
             nullptr, nullptr, nb, in, side, d_tau, d_charge, d_done, lv, out);
         SP_CHECK_LAUNCH();
@@ -140,13 +150,13 @@ static size_t level_buf_elems(const spamm_mat* A) {
     return (size_t)(s * s * s);
 }
 
-int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau_ptr,
-             double* d_err, const double* d_charge) {
+int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
+             const double* d_tau_ptr, double* d_err, const ChargeData& d_charge) {
     size_t e = level_buf_elems(A);
     double *b0 = nullptr, *b1 = nullptr;
     SP_TRY(dalloc((void**)&b0, sizeof(double) * e, ctx->stream));
     SP_TRY(dalloc((void**)&b1, sizeof(double) * e, ctx->stream));
-    int st = cse_eval_impl(ctx, A, B, d_tau_ptr, nullptr, d_err, d_charge, b0, b1);
+    int st = cse_eval_impl(ctx, A, nA, nB, d_tau_ptr, nullptr, d_err, d_charge, b0, b1);
     dfree(b0, ctx->stream);
     dfree(b1, ctx->stream);
     return st;
@@ -180,8 +190,8 @@ __global__ void k_bisect_step(DevScalars* sc, const double* __restrict__ tau, do
     }
 }
 
-int cse_search(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double delta,
-               const double* d_charge, int* evals) {
+int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
+               double delta, const ChargeData& d_charge, int* evals) {
     cudaStream_t s = ctx->stream;
     DevScalars* sc = (DevScalars*)ctx->d_scalars;
     size_t e = level_buf_elems(A);
@@ -191,11 +201,13 @@ int cse_search(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double de
     const int N = SPAMM_N_TAU;
     int steps = 0;
     while ((1 << steps) < N + 1) ++steps;
+    ++ctx->launches;
     k_bisect_init<<<1, 1, 0, s>>>(sc, ctx->d_tau, N);
     int st = SPAMM_OK;
     for (int it = 0; it < steps && st == SPAMM_OK; ++it) {
-        st = cse_eval_impl(ctx, A, B, &sc->tau_mid, &sc->done, &sc->err_mid, d_charge, b0, b1);
+        st = cse_eval_impl(ctx, A, nA, nB, &sc->tau_mid, &sc->done, &sc->err_mid, d_charge, b0, b1);
         if (st == SPAMM_OK) {
+            ++ctx->launches;
             k_bisect_step<<<1, 1, 0, s>>>(sc, ctx->d_tau, delta);
             st = cudaGetLastError() == cudaSuccess ? SPAMM_OK : SPAMM_ECUDA;
         }
@@ -204,6 +216,21 @@ int cse_search(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, double de
     dfree(b1, s);
     if (evals) *evals = steps;
     return st;
+}
+
+__global__ void k_sym_norms(const double* __restrict__ in, int nb, double* __restrict__ out) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)nb * nb) return;
+    const int i = (int)(b / nb), j = (int)(b % nb);
+    out[b] = i <= j ? in[b] : in[(int64_t)j * nb + i];
+}
+
+int sym_norms(spamm_ctx* ctx, const double* in, int nb, double* out) {
+    const int64_t nb2 = (int64_t)nb * nb;
+    ++ctx->launches;
+    k_sym_norms<<<(unsigned)((nb2 + 255) / 256), 256, 0, ctx->stream>>>(in, nb, out);
+    SP_CHECK_LAUNCH();
+    return SPAMM_OK;
 }
 
 }  // namespace spamm
@@ -226,7 +253,8 @@ extern "C" int spamm_cse(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B,
     SP_TRY(dalloc((void**)&b0, sizeof(double) * e, s));
     SP_TRY(dalloc((void**)&b1, sizeof(double) * e, s));
     for (int t = 0; t < N; ++t)
-        SP_TRY(cse_eval_impl(ctx, A, B, d + t, nullptr, d + N + t, nullptr, b0, b1));
+        SP_TRY(cse_eval_impl(ctx, A, A->d_norm, B->d_norm, d + t, nullptr, d + N + t, ChargeData(),
+                             b0, b1));
     SP_CUDA(cudaMemcpyAsync(errors, d + N, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
     SP_CUDA(cudaStreamSynchronize(s));
     dfree(b0, s);

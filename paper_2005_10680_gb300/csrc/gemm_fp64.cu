@@ -26,7 +26,8 @@ __global__ void __launch_bounds__(256)
 k_gemm_fp64(const double* __restrict__ tilesA, const double* __restrict__ tilesB,
             const int32_t* __restrict__ task_a, const int32_t* __restrict__ task_b,
             const int32_t* __restrict__ work_ij, const int32_t* __restrict__ work_out,
-            const int64_t* __restrict__ work_off, int nb, int mode,
+            const int32_t* __restrict__ work_out_t, const int64_t* __restrict__ work_off, int nb,
+            int mode,
             const int32_t* __restrict__ mapX, const double* __restrict__ tilesX,
             double* __restrict__ tilesC, double* __restrict__ normC,
             double* __restrict__ part_fro2, double* __restrict__ part_trace,
@@ -85,6 +86,10 @@ k_gemm_fp64(const double* __restrict__ tilesA, const double* __restrict__ tilesB
         if (xs >= 0) X = tilesX + (int64_t)xs * BS * BS;
     }
     double* Cout = os >= 0 ? tilesC + (int64_t)os * BS * BS : nullptr;
+    // symmetric mode: the mirror block (j, i) receives the transpose
+    const int32_t ost = work_out_t ? work_out_t[w] : -1;
+    double* Cout_t = ost >= 0 ? tilesC + (int64_t)ost * BS * BS : nullptr;
+    const double mult = (work_out_t && bi != bj) ? 2.0 : 1.0;
     double fro2 = 0.0, tr = 0.0, idem2 = 0.0;
 #pragma unroll
     for (int r = 0; r < TM; ++r)
@@ -102,6 +107,7 @@ k_gemm_fp64(const double* __restrict__ tilesA, const double* __restrict__ tilesB
             fro2 = fma(out, out, fro2);
             if (bi == bj && row == col) tr += out;
             if (Cout) Cout[row * BS + col] = out;
+            if (Cout_t) Cout_t[col * BS + row] = out;
         }
     red[0][tid] = fro2;
     red[1][tid] = tr;
@@ -116,10 +122,12 @@ k_gemm_fp64(const double* __restrict__ tilesA, const double* __restrict__ tilesB
         __syncthreads();
     }
     if (tid == 0) {
-        part_fro2[w] = red[0][0];
+        part_fro2[w] = mult * red[0][0];
         part_trace[w] = red[1][0];
-        part_idem2[w] = red[2][0];
-        if (os >= 0) normC[ij] = sqrt(red[0][0]);
+        part_idem2[w] = mult * red[2][0];
+        const double nrm = sqrt(red[0][0]);
+        if (os >= 0) normC[ij] = nrm;
+        if (ost >= 0) normC[(int64_t)bj * nb + bi] = nrm;
     }
 }
 
@@ -133,9 +141,11 @@ int gemm_fp64(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const Plan
     const unsigned G = (unsigned)plan.n_work;
 #define SP_GEMM_LAUNCH(BSV)                                                                    \
     k_gemm_fp64<BSV><<<G, 256, 0, s>>>(A->d_tiles, B->d_tiles, plan.d_task_a, plan.d_task_b,  \
-                                       plan.d_work_ij, plan.d_work_out, plan.d_work_off,      \
-                                       plan.nb, ep.mode, mapX, tilesX, C->d_tiles, C->d_norm, \
+                                       plan.d_work_ij, plan.d_work_out, plan.d_work_out_t,   \
+                                       plan.d_work_off, plan.nb, ep.mode, mapX, tilesX,       \
+                                       C->d_tiles, C->d_norm,                                 \
                                        d_part_fro2, d_part_trace, d_part_idem2)
+    ++ctx->launches;
     switch (A->bs) {
         case 32: SP_GEMM_LAUNCH(32); break;
         case 64: SP_GEMM_LAUNCH(64); break;

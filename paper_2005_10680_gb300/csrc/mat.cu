@@ -136,8 +136,11 @@ int scan_i32_to_i64(spamm_ctx* ctx, const int32_t* d_in, int64_t* d_out, int64_t
     int64_t nblk = (count + SCAN_TILE - 1) / SCAN_TILE;
     long long* sums = nullptr;
     SP_TRY(dalloc((void**)&sums, sizeof(long long) * nblk, s));
+    ++ctx->launches;
     k_scan_reduce<<<(unsigned)nblk, SCAN_T, 0, s>>>(d_in, count, sums);
+    ++ctx->launches;
     k_scan_sums<<<1, SCAN_T, 0, s>>>(sums, nblk, d_total);
+    ++ctx->launches;
     k_scan_apply<<<(unsigned)nblk, SCAN_T, 0, s>>>(d_in, count, sums, d_out);
     dfree(sums, s);
     SP_CHECK_LAUNCH();
@@ -149,6 +152,8 @@ int scan_i32_to_i64(spamm_ctx* ctx, const int32_t* d_in, int64_t* d_out, int64_t
 int mat_alloc(spamm_ctx* ctx, int64_t n, int bs, int64_t cap, spamm_mat** out) {
     spamm_mat* m = new spamm_mat();
     memset(m, 0, sizeof(*m));
+    m->ctx = ctx;
+    ctx->refs++;
     m->device = ctx->device;
     m->stream = ctx->stream;
     m->n = n;
@@ -239,6 +244,7 @@ int mat_compute_norms(spamm_ctx* ctx, spamm_mat* m) {
     if (m->nslots == 0) return SPAMM_OK;
     int64_t threads = m->nslots * 32;
     int blocks = (int)((threads + 255) / 256);
+    ++ctx->launches;
     k_tile_norms<<<blocks, 256, 0, ctx->stream>>>(m->d_tiles, m->d_coord, m->nslots, m->bs,
                                                    m->d_norm);
     SP_CHECK_LAUNCH();
@@ -286,6 +292,7 @@ __global__ void k_trace(const double* __restrict__ tiles, const int32_t* __restr
 }
 
 int mat_trace(spamm_ctx* ctx, const spamm_mat* X, double* d_out) {
+    ++ctx->launches;
     k_trace<<<1, 128, 0, ctx->stream>>>(X->d_tiles, X->d_map, X->nb, X->bs, d_out);
     SP_CHECK_LAUNCH();
     return SPAMM_OK;
@@ -322,6 +329,7 @@ __global__ void k_reduce3(const double* __restrict__ a, const double* __restrict
 
 int reduce_partials(spamm_ctx* ctx, const double* d_fro2, const double* d_trace,
                     const double* d_idem2, int64_t count) {
+    ++ctx->launches;
     k_reduce3<<<1, 1024, 0, ctx->stream>>>(d_fro2, d_trace, d_idem2, count,
                                             (DevScalars*)ctx->d_scalars);
     SP_CHECK_LAUNCH();
@@ -362,6 +370,7 @@ extern "C" int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, 
     SP_TRY(dalloc((void**)&slot, sizeof(int64_t) * (nb2 + 1), s));
     SP_TRY(dalloc((void**)&d_tot, sizeof(unsigned long long), s));
     dim3 grid(nb, nb);
+    ++ctx->launches;
     k_block_present<<<grid, 256, 0, s>>>(src, n, ld, bs, nb, drop_abs, present);
     SP_CHECK_LAUNCH();
     SP_TRY(scan_i32_to_i64(ctx, present, slot, nb2, d_tot));
@@ -372,6 +381,7 @@ extern "C" int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, 
     SP_TRY(mat_alloc(ctx, n, bs, (int64_t)nnzb, &m));
     m->nslots = (int64_t)nnzb;
     m->nnzb = (int64_t)nnzb;
+    ++ctx->launches;
     k_fill_tiles<<<grid, 256, 0, s>>>(src, n, ld, bs, nb, drop_abs, present, slot, m->d_map,
                                       m->d_coord, m->d_tiles);
     SP_CHECK_LAUNCH();
@@ -405,10 +415,13 @@ extern "C" int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* ou
         dst = staged;
         dld = m->n;
     }
+    ++ctx->launches;
     k_zero_rows<<<(unsigned)m->n, 256, 0, s>>>(dst, m->n, dld);
-    if (m->nslots)
+    if (m->nslots) {
+        ++ctx->launches;
         k_scatter_dense<<<(unsigned)m->nslots, 256, 0, s>>>(m->d_tiles, m->d_coord, m->bs, m->nb,
                                                             m->n, dst, dld);
+    }
     SP_CHECK_LAUNCH();
     if (!out_on_device) {
         SP_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * ld, staged, sizeof(double) * m->n,
@@ -462,5 +475,10 @@ extern "C" void spamm_mat_free(spamm_mat* m) {
     dfree(m->d_coord, m->stream);
     dfree(m->d_tiles, m->stream);
     dfree(m->d_rowabs, m->stream);
+    spamm_ctx* ctx = m->ctx;
     delete m;
+    if (ctx) {
+        ctx->refs--;
+        ctx_release(ctx);
+    }
 }

@@ -1,0 +1,788 @@
+// Mixed-precision leaf products: float64-accurate products of float64 leaf
+// blocks on the bf16 tensor cores (tcgen05), with the rounding of every kept
+// product charged inside the Algorithm 3 bound.
+//
+// Slicing. Every row r of the left operand gets an exponent e_r with
+// max_c |A[r,c]| < 2^e_r (every column s of the right operand an f_s). An
+// entry becomes signed 7-bit digits: r_0 = A[r,c] / 2^e_r, and for p = 1..8
+// a_p = rint(128 r_{p-1}), r_p = 128 r_{p-1} - a_p, so that
+//     A = sum_p A_p + T_8,  A_p[r,c] = a_p 2^(e_r - 7p),  |a_1| <= 128, |a_p| <= 64,
+// every digit exact in bf16. The slices are stored per leaf block in the
+// K-major, no-swizzle layout that the tensor core reads (8-row x 16-byte core
+// matrices), so a 2 KB chunk (64 rows x 16 K) moves with one bulk copy.
+//
+// Exact accumulation. Products of digits are integers below 2^14 in units of
+// 2^(e_r + f_s - 7(p+q)); grouping them by level L = p + q, one level's sum over
+// one leaf product (K = 64) stays below 2^18 (L + 1) <= 2^21.3 for L <= 9, so
+// T = 6 leaf products fit below 2^24 and the f32 accumulators hold them
+// exactly. Every T products the 8 level accumulators (all 512 TMEM columns)
+// are folded into two int64 words per entry, V = H 2^28 + Lo with
+// V = sum_L G_L 2^(7(Lmax - L)), and zeroed.
+//
+// Charge. Forming only the pairs p + q <= L leaves the error
+//     A B - sum_{p+q<=L} A_p B_q = sum_{p=1}^{L-1} A_p T^B_{L-p} + T^A_{L-1} B,
+// bounded by c = sum_p ||A_p||_F ||T^B_{L-p}||_F + ||T^A_{L-1}||_F ||B||_F per
+// product (slice and tail norms are kept per block). A kept triple contributes
+// min(c, ||A_ik|| ||B_kj||) to Algorithm 3's leaf in place of 0; when c is not
+// below the norm product the product is not formed at all (its error is then
+// at most the norm product). The recursion of Algorithm 3 is unchanged, so the
+// bound it returns covers skipped products and slicing together.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace spamm {
+
+constexpr int MX_W = 7;
+constexpr int MX_S = 8;
+constexpr int MX_LMAX = 9;
+constexpr int MX_BS = 64;
+constexpr int CHUNK = 2048;                      // 64 rows x 16 K x 2 bytes
+constexpr int SLICE_BYTES = 4 * CHUNK;           // one slice of one 64 x 64 block
+constexpr int TILE_BYTES = MX_S * SLICE_BYTES;   // all slices of one block (64 KB)
+
+// ------------------------------------------------------------- slicing
+
+// rows (transpose = 0) or columns (transpose = 1) maxima of every stored block
+__global__ void k_block_rowmax(const double* __restrict__ tiles, const int32_t* __restrict__ coord,
+                               int transpose, float* __restrict__ out_unused,
+                               double* __restrict__ rmax) {
+    const int64_t s = blockIdx.x;
+    const int t = threadIdx.x;   // 256
+    __shared__ double sh[4][64];
+    const double* T = tiles + s * MX_BS * MX_BS;
+    if (coord[s] < 0) {
+        if (t < 64) rmax[s * 64 + t] = 0.0;
+        return;
+    }
+    double m = 0.0;
+    if (!transpose) {
+        const int row = t >> 2, q = t & 3;
+        for (int c = q * 16; c < q * 16 + 16; ++c) m = fmax(m, fabs(T[row * MX_BS + c]));
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        if (q == 0) rmax[s * 64 + row] = m;
+    } else {
+        const int col = t & 63, q = t >> 6;
+        for (int r = q * 16; r < q * 16 + 16; ++r) m = fmax(m, fabs(T[r * MX_BS + col]));
+        sh[q][col] = m;
+        __syncthreads();
+        if (t < 64) rmax[s * 64 + t] = fmax(fmax(sh[0][t], sh[1][t]), fmax(sh[2][t], sh[3][t]));
+    }
+}
+
+// exponent of every row (columns when transpose): max |x| < 2^e
+__global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __restrict__ map,
+                            int nb, int transpose, int32_t* __restrict__ expo) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= (int64_t)nb * MX_BS) return;
+    const int rb = (int)(r / MX_BS), rr = (int)(r % MX_BS);
+    double m = 0.0;
+    for (int o = 0; o < nb; ++o) {
+        const int32_t s = transpose ? map[(int64_t)o * nb + rb] : map[(int64_t)rb * nb + o];
+        if (s >= 0) m = fmax(m, rmax[(int64_t)s * 64 + rr]);
+    }
+    int e = 0;
+    if (m > 0.0) frexp(m, &e);   // m = f 2^e, f in [0.5, 1): m < 2^e
+    expo[r] = e;
+}
+
+// One CTA (256 threads) per stored block: digits, leading-zero slice, slice and
+// tail norms. transpose: slice the transposed block with column exponents.
+__global__ void __launch_bounds__(256)
+k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
+        const int32_t* __restrict__ expo, uint8_t* __restrict__ slices, int8_t* __restrict__ p0,
+        double* __restrict__ sn, double* __restrict__ tn) {
+    const int64_t s = blockIdx.x;
+    const int t = threadIdx.x;
+    __shared__ double T[MX_BS][MX_BS + 1];
+    __shared__ double red_a[8][MX_S], red_r[8][MX_S];
+    __shared__ int first;
+    const int32_t cd = coord[s];
+    if (t == 0) first = MX_S + 1;
+    const double* G = tiles + s * MX_BS * MX_BS;
+    for (int e = t; e < MX_BS * MX_BS; e += 256) {
+        const int r = e / MX_BS, c = e % MX_BS;
+        if (transpose) T[c][r] = G[e];
+        else T[r][c] = G[e];
+    }
+    __syncthreads();
+    if (cd < 0) return;
+    const int bi = cd / nb, bj = cd % nb;
+    // the block's rows are rows of block-row bi (columns of block-column bj when transposed)
+    const int base = (transpose ? bj : bi) * MX_BS;
+    const int row = t >> 2, kq = t & 3;           // kq: two groups of 8 K values each
+    const int e_r = expo[base + row];
+    double sa[MX_S], sr[MX_S];
+#pragma unroll
+    for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.0;
+    int firstp = MX_S + 1;
+    uint8_t* out = slices + s * (int64_t)TILE_BYTES;
+#pragma unroll
+    for (int g2 = 0; g2 < 2; ++g2) {
+        const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
+        double rem[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) rem[e] = ldexp(T[row][kg * 8 + e], -e_r);
+#pragma unroll
+        for (int p = 0; p < MX_S; ++p) {
+            uint32_t packed[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                double t0 = rem[e] * 128.0, t1 = rem[e + 1] * 128.0;
+                double a0 = rint(t0), a1 = rint(t1);
+                rem[e] = t0 - a0;
+                rem[e + 1] = t1 - a1;
+                sa[p] = fma(a0, a0, fma(a1, a1, sa[p]));
+                if ((a0 != 0.0 || a1 != 0.0) && p + 1 < firstp) firstp = p + 1;
+                __nv_bfloat16 b0 = __float2bfloat16_rn((float)a0), b1 = __float2bfloat16_rn((float)a1);
+                packed[e / 2] = (uint32_t)__bfloat16_as_ushort(b0) |
+                                ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+            }
+#pragma unroll
+            for (int e = 0; e < 8; ++e) sr[p] = fma(rem[e], rem[e], sr[p]);
+            // canonical offset: slice p, chunk kg/2, group row/8, k-core kg%2, row%8
+            const int off = p * SLICE_BYTES + (kg >> 1) * CHUNK + (row >> 3) * 256 + (kg & 1) * 128 +
+                            (row & 7) * 16;
+            *reinterpret_cast<uint4*>(out + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        }
+    }
+    // scale by 2^(2(e_r - 7p)) and reduce over the block (fixed order)
+#pragma unroll
+    for (int p = 0; p < MX_S; ++p) {
+        const double sc = ldexp(1.0, 2 * (e_r - MX_W * (p + 1)));
+        double a = sa[p] * sc, r = sr[p] * sc;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            r += __shfl_xor_sync(0xffffffffu, r, o);
+        }
+        if ((t & 31) == 0) {
+            red_a[t >> 5][p] = a;
+            red_r[t >> 5][p] = r;
+        }
+    }
+    atomicMin(&first, firstp);
+    __syncthreads();
+    if (t < MX_S) {
+        double a = 0.0, r = 0.0;
+        for (int w = 0; w < 8; ++w) {
+            a += red_a[w][t];
+            r += red_r[w][t];
+        }
+        sn[s * MX_S + t] = sqrt(a);
+        tn[s * MX_S + t] = sqrt(r);
+    }
+    if (t == 0) p0[s] = (int8_t)first;
+}
+
+struct SliceSet {
+    uint8_t* slices = nullptr;
+    int8_t* p0 = nullptr;
+    double* sn = nullptr;
+    double* tn = nullptr;
+    int32_t* expo = nullptr;
+    void free(cudaStream_t s) {
+        dfree(slices, s);
+        dfree(p0, s);
+        dfree(sn, s);
+        dfree(tn, s);
+        dfree(expo, s);
+    }
+};
+
+static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, SliceSet* out) {
+    cudaStream_t s = ctx->stream;
+    const int64_t ns = X->nslots > 0 ? X->nslots : 1;
+    SP_TRY(dalloc((void**)&out->slices, (size_t)ns * TILE_BYTES, s));
+    SP_TRY(dalloc((void**)&out->p0, (size_t)ns, s));
+    SP_TRY(dalloc((void**)&out->sn, sizeof(double) * ns * MX_S, s));
+    SP_TRY(dalloc((void**)&out->tn, sizeof(double) * ns * MX_S, s));
+    SP_TRY(dalloc((void**)&out->expo, sizeof(int32_t) * (size_t)X->nb * MX_BS, s));
+    double* rmax = nullptr;
+    SP_TRY(dalloc((void**)&rmax, sizeof(double) * ns * 64, s));
+    if (X->nslots > 0) {
+        ++ctx->launches;
+        k_block_rowmax<<<(unsigned)X->nslots, 256, 0, s>>>(X->d_tiles, X->d_coord, transpose,
+                                                           nullptr, rmax);
+    }
+    const int64_t rows = (int64_t)X->nb * MX_BS;
+    ++ctx->launches;
+    k_exponents<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(rmax, X->d_map, X->nb, transpose,
+                                                               out->expo);
+    if (X->nslots > 0) {
+        ++ctx->launches;
+        k_split<<<(unsigned)X->nslots, 256, 0, s>>>(X->d_tiles, X->d_coord, X->nb, transpose,
+                                                    out->expo, out->slices, out->p0, out->sn,
+                                                    out->tn);
+    }
+    SP_CHECK_LAUNCH();
+    dfree(rmax, s);
+    return SPAMM_OK;
+}
+
+// ------------------------------------------------------------ planning
+
+// Work item: a pair of block rows {2I, 2I+1} times block column j (M = 128).
+// Task: (slot of A_{2I,k} or -1, slot of A_{2I+1,k} or -1, slot of the B operand).
+__device__ __forceinline__ bool mx_keep(const ChargeData& ch, int i, int k, int j, double tau,
+                                        int32_t* sa, int32_t* sb) {
+    const int nb = ch.nb;
+    *sa = ch.mapA[(int64_t)i * nb + k];
+    *sb = ch.bt_from_a ? ch.mapA[(int64_t)j * nb + k] : ch.mapB[(int64_t)k * nb + j];
+    const int32_t pb = ch.bt_from_a ? *sb : ch.mapB[(int64_t)k * nb + j];
+    if (*sa < 0 || pb < 0) return false;
+    const double p = ch.nA[(int64_t)i * nb + k] * ch.nB[(int64_t)k * nb + j];
+    if (p < tau) return false;
+    return charge(ch, *sa, *sb, ch.nB[(int64_t)k * nb + j]) < p;
+}
+
+__global__ void k_pair_count(ChargeData ch, const int32_t* __restrict__ out_flag,
+                             const int32_t* __restrict__ mapX, int sym,
+                             const double* __restrict__ d_tau, int32_t* __restrict__ cnt,
+                             int32_t* __restrict__ wflag) {
+    const int nb = ch.nb, np = (nb + 1) / 2;
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= (int64_t)np * nb) return;
+    const int I = (int)(b / nb), j = (int)(b % nb);
+    const int i0 = 2 * I, i1 = 2 * I + 1;
+    int c = 0, work = 0;
+    if (!sym || i0 <= j) {
+        const double tau = *d_tau;
+        for (int k = 0; k < nb; ++k) {
+            int32_t sa, sb;
+            bool kt = mx_keep(ch, i0, k, j, tau, &sa, &sb);
+            bool kb = (i1 < nb) && mx_keep(ch, i1, k, j, tau, &sa, &sb);
+            if (kt || kb) ++c;
+        }
+        const int64_t b0 = (int64_t)i0 * nb + j, b1 = (int64_t)i1 * nb + j;
+        work = out_flag[b0] || (mapX && mapX[b0] >= 0);
+        if (i1 < nb) work = work || out_flag[b1] || (mapX && mapX[b1] >= 0);
+    }
+    cnt[b] = work ? c : 0;
+    wflag[b] = work;
+}
+
+__device__ __forceinline__ int n_level_pairs(int pa, int qb, int L) {
+    int n = 0;
+    for (int p = pa; p <= MX_S && p + qb <= L; ++p) n += min(MX_S, L - p) - qb + 1;
+    return n;
+}
+
+__global__ void k_pair_fill(ChargeData ch, const int32_t* __restrict__ out_flag,
+                            const int64_t* __restrict__ out_idx, int sym,
+                            const double* __restrict__ d_tau, const int32_t* __restrict__ wflag,
+                            const int64_t* __restrict__ widx, const int64_t* __restrict__ toff,
+                            int32_t* __restrict__ work_ij, int32_t* __restrict__ work_out,
+                            int64_t* __restrict__ work_off, int32_t* __restrict__ task,
+                            const int8_t* __restrict__ p0A, const int8_t* __restrict__ p0B,
+                            unsigned long long* __restrict__ counters) {
+    const int nb = ch.nb, np = (nb + 1) / 2;
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long formed = 0, pairs = 0;
+    if (b < (int64_t)np * nb && wflag[b]) {
+        const int I = (int)(b / nb), j = (int)(b % nb);
+        const int i0 = 2 * I, i1 = 2 * I + 1;
+        const int64_t w = widx[b];
+        work_ij[w] = (int32_t)b;
+        const int64_t b0 = (int64_t)i0 * nb + j, b1 = (int64_t)i1 * nb + j;
+        int32_t* wo = work_out + 4 * w;   // top, bottom, top mirror, bottom mirror
+        wo[0] = out_flag[b0] ? (int32_t)out_idx[b0] : -1;
+        wo[1] = (i1 < nb && out_flag[b1]) ? (int32_t)out_idx[b1] : -1;
+        const bool mir = sym && j > i1;
+        wo[2] = (mir && out_flag[(int64_t)j * nb + i0]) ? (int32_t)out_idx[(int64_t)j * nb + i0] : -1;
+        wo[3] = (mir && out_flag[(int64_t)j * nb + i1]) ? (int32_t)out_idx[(int64_t)j * nb + i1] : -1;
+        int64_t t = toff[b];
+        work_off[w] = t;
+        const double tau = *d_tau;
+        for (int k = 0; k < nb; ++k) {
+            int32_t sa0, sb0, sa1 = -1, sb1;
+            bool kt = mx_keep(ch, i0, k, j, tau, &sa0, &sb0);
+            bool kb = (i1 < nb) && mx_keep(ch, i1, k, j, tau, &sa1, &sb1);
+            if (!(kt || kb)) continue;
+            const int32_t s0 = kt ? sa0 : -1, s1 = kb ? sa1 : -1, sb = kt ? sb0 : sb1;
+            task[3 * t + 0] = s0;
+            task[3 * t + 1] = s1;
+            task[3 * t + 2] = sb;
+            formed += (kt ? 1 : 0) + (kb ? 1 : 0);
+            const int pa = min(s0 >= 0 ? (int)p0A[s0] : MX_S + 1, s1 >= 0 ? (int)p0A[s1] : MX_S + 1);
+            pairs += n_level_pairs(pa, p0B[sb], ch.lmax);
+            ++t;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        formed += __shfl_xor_sync(0xffffffffu, formed, o);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    }
+    if ((threadIdx.x & 31) == 0 && formed) {
+        atomicAdd(counters, formed);
+        atomicAdd(counters + 1, pairs);
+    }
+}
+
+__global__ void k_last_off(int64_t* work_off, int64_t n_work, const int64_t* toff, int64_t n) {
+    work_off[n_work] = toff[n];
+}
+
+// ------------------------------------------------------ the tcgen05 kernel
+
+constexpr int GM_STAGES = 4;
+constexpr int STAGE_A = MX_S * 2 * CHUNK;   // 8 slices x (two 64-row chunks)
+constexpr int STAGE_B = MX_S * CHUNK;
+constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
+constexpr int GM_THREADS = 18 * 32;         // warp 0 copies, warp 1 issues MMAs, 16 fold/epilogue
+constexpr int GM_SMEM = GM_STAGES * STAGE_BYTES + 1024;
+constexpr long long WAIT_LIMIT = 1ll << 22;
+
+struct MixedArgs {
+    const uint8_t* slA;
+    const uint8_t* slB;
+    const int8_t* p0A;
+    const int8_t* p0B;
+    const int32_t* expA;
+    const int32_t* expB;
+    const uint8_t* zero_chunk;   // CHUNK bytes of zeros
+    const int32_t* task;         // [3 * n_tasks]
+    const int32_t* work_ij;
+    const int32_t* work_out;     // [4 * n_work]
+    const int64_t* work_off;
+    int nb;
+    int lmax;
+    int window;                  // leaf products per exact-accumulation window
+    int mode;                    // 0: C; 1: Xn = C; 2: Xn = 2X - C
+    const int32_t* mapX;
+    const double* tilesX;
+    double* tilesC;
+    double* normC;
+    double* part_fro2;           // [2 * n_work]
+    double* part_trace;
+    double* part_idem2;
+    int* status;
+};
+
+__device__ __forceinline__ int tile_p0(const int8_t* p0, int32_t s) { return s >= 0 ? p0[s] : MX_S + 1; }
+
+__global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* stages = smem;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + GM_STAGES * STAGE_BYTES);
+    // bars: full[4], empty[4], acc_full, acc_empty, drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
+    volatile int* s_err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    double* red = reinterpret_cast<double*>(smem + GM_STAGES * STAGE_BYTES + 128);   // [16][3]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int w = blockIdx.x;
+    const int64_t t0 = a.work_off[w], t1 = a.work_off[w + 1];
+    const int ntask = (int)(t1 - t0);
+    const int nwin = (ntask + a.window - 1) / a.window;
+    const int L = a.lmax;
+    const uint32_t b_full = tc::smem_u32(bars), b_empty = tc::smem_u32(bars + 4);
+    const uint32_t b_accf = tc::smem_u32(bars + 8), b_acce = tc::smem_u32(bars + 9);
+    const uint32_t b_drain = tc::smem_u32(bars + 10);
+    if (tid == 0) {
+        for (int i = 0; i < GM_STAGES; ++i) {
+            tc::mbar_init(b_full + 8 * i, 1);
+            tc::mbar_init(b_empty + 8 * i, 1);
+        }
+        tc::mbar_init(b_accf, 1);
+        tc::mbar_init(b_acce, 16);
+        tc::mbar_init(b_drain, 1);
+        *s_err = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) tc::tmem_alloc(tc::smem_u32(tmem_slot), 512);
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ producer (one lane)
+        if (lane == 0) {
+            int it = 0;
+            for (int64_t t = t0; t < t1 && !*s_err; ++t) {
+                const int32_t s0 = a.task[3 * t], s1 = a.task[3 * t + 1], sb = a.task[3 * t + 2];
+                const int pa = min(tile_p0(a.p0A, s0), tile_p0(a.p0A, s1));
+                const int qb = tile_p0(a.p0B, sb);
+                const int pmax = min(MX_S, L - qb), qmax = min(MX_S, L - pa);
+                for (int c = 0; c < 4; ++c, ++it) {
+                    const int st = it % GM_STAGES;
+                    if (!tc::mbar_wait(b_empty + 8 * st, ((it / GM_STAGES) & 1) ^ 1, WAIT_LIMIT)) {
+                        atomicExch((int*)s_err, 1);
+                        break;
+                    }
+                    const int np = pmax >= pa ? pmax - pa + 1 : 0;
+                    const int nq = qmax >= qb ? qmax - qb + 1 : 0;
+                    tc::mbar_arrive_expect_tx(b_full + 8 * st, (uint32_t)(2 * np + nq) * CHUNK);
+                    const uint32_t sA = tc::smem_u32(stages + st * STAGE_BYTES);
+                    const uint32_t sB = sA + STAGE_A;
+                    for (int p = pa; p <= pmax; ++p) {
+                        const uint8_t* g0 = s0 >= 0 ? a.slA + (int64_t)s0 * TILE_BYTES +
+                                                          (p - 1) * SLICE_BYTES + c * CHUNK
+                                                    : a.zero_chunk;
+                        const uint8_t* g1 = s1 >= 0 ? a.slA + (int64_t)s1 * TILE_BYTES +
+                                                          (p - 1) * SLICE_BYTES + c * CHUNK
+                                                    : a.zero_chunk;
+                        tc::bulk_g2s(sA + (p - 1) * 2 * CHUNK, g0, CHUNK, b_full + 8 * st);
+                        tc::bulk_g2s(sA + (p - 1) * 2 * CHUNK + CHUNK, g1, CHUNK, b_full + 8 * st);
+                    }
+                    for (int q = qb; q <= qmax; ++q)
+                        tc::bulk_g2s(sB + (q - 1) * CHUNK,
+                                     a.slB + (int64_t)sb * TILE_BYTES + (q - 1) * SLICE_BYTES + c * CHUNK,
+                                     CHUNK, b_full + 8 * st);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (one lane)
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+            int it = 0;
+            int64_t t = t0;
+            for (int win = 0; win < nwin && !*s_err; ++win) {
+                if (!tc::mbar_wait(b_acce, win & 1, WAIT_LIMIT)) {
+                    atomicExch((int*)s_err, 2);
+                    break;
+                }
+                tc::fence_after();
+                const int64_t tend = min(t1, t + a.window);
+                for (; t < tend && !*s_err; ++t) {
+                    const int32_t s0 = a.task[3 * t], s1 = a.task[3 * t + 1], sb = a.task[3 * t + 2];
+                    const int pa = min(tile_p0(a.p0A, s0), tile_p0(a.p0A, s1));
+                    const int qb = tile_p0(a.p0B, sb);
+                    for (int c = 0; c < 4; ++c, ++it) {
+                        const int st = it % GM_STAGES;
+                        if (!tc::mbar_wait(b_full + 8 * st, (it / GM_STAGES) & 1, WAIT_LIMIT)) {
+                            atomicExch((int*)s_err, 3);
+                            break;
+                        }
+                        tc::fence_after();
+                        const uint32_t sA = tc::smem_u32(stages + st * STAGE_BYTES);
+                        const uint32_t sB = sA + STAGE_A;
+                        for (int p = pa; p <= MX_S && p + qb <= L; ++p)
+                            for (int q = qb; q <= MX_S && p + q <= L; ++q) {
+                                const uint64_t da = tc::desc_kmajor(sA + (p - 1) * 2 * CHUNK, 128, 256);
+                                const uint64_t db = tc::desc_kmajor(sB + (q - 1) * CHUNK, 128, 256);
+                                tc::mma_bf16(tmem + (uint32_t)(p + q - 2) * 64, da, db, idesc, 1u);
+                            }
+                        tc::commit(b_empty + 8 * st);
+                    }
+                }
+                tc::commit(b_accf);
+            }
+            tc::commit(b_drain);
+            if (!tc::mbar_wait(b_drain, 0, WAIT_LIMIT)) atomicExch((int*)s_err, 4);
+        }
+    } else {
+        // ------------------------------------------ fold + epilogue (16 warps)
+        const int ew = warp - 2;
+        const int quarter = warp & 3;           // TMEM lanes 32*quarter .. +31
+        const int cb = ew >> 2;                 // columns 16*cb .. +15
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cb * 16);
+        long long H[16], Lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) H[j] = Lo[j] = 0;
+        for (int lv = 2; lv <= L; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - 2) * 64);
+        tc::tmem_st_wait();
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(b_acce);
+        for (int win = 0; win < nwin; ++win) {
+            if (__any_sync(0xffffffffu, *s_err != 0)) break;
+            const bool ok = tc::mbar_wait(b_accf, win & 1, WAIT_LIMIT);
+            if (!__all_sync(0xffffffffu, ok)) {     // warp-uniform: tcgen05.ld/st are .aligned
+                if (lane == 0) atomicExch((int*)s_err, 5);
+                break;
+            }
+            tc::fence_after();
+            for (int lv = 2; lv <= L; ++lv) {
+                uint32_t v[16];
+                tc::tmem_ld16(trow + (uint32_t)(lv - 2) * 64, v);
+                tc::tmem_ld_wait();
+                const int sh = MX_W * (L - lv);     // weight of this level in V
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const long long g = (long long)__float2int_rn(__uint_as_float(v[j]));
+                    if (sh < 28) Lo[j] += g << sh;
+                    else H[j] += g << (sh - 28);
+                }
+            }
+            for (int lv = 2; lv <= L; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - 2) * 64);
+            tc::tmem_st_wait();
+            tc::fence_before();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(b_acce);
+        }
+        // ---- values, SP2 combination, writes, partial sums
+        const int nb = a.nb;
+        const int32_t ij = a.work_ij[w];
+        const int I = ij / nb, jb = ij % nb;
+        const int rl = quarter * 32 + lane;      // 0..127
+        const int half = rl >> 6, rr = rl & 63;
+        const int bi = 2 * I + half;
+        const int32_t os = a.work_out[4 * w + half];
+        const int32_t ost = a.work_out[4 * w + 2 + half];
+        double fro2 = 0.0, tr = 0.0, idem2 = 0.0;
+        if (bi < nb) {
+            const int er = a.expA[bi * MX_BS + rr];
+            const double* X = nullptr;
+            if (a.mode != 0 && a.mapX) {
+                const int32_t xs = a.mapX[(int64_t)bi * nb + jb];
+                if (xs >= 0) X = a.tilesX + (int64_t)xs * MX_BS * MX_BS;
+            }
+            double* Co = os >= 0 ? a.tilesC + (int64_t)os * MX_BS * MX_BS : nullptr;
+            double* Ct = ost >= 0 ? a.tilesC + (int64_t)ost * MX_BS * MX_BS : nullptr;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int sc = cb * 16 + j;
+                const int fs = a.expB[jb * MX_BS + sc];
+                const double v = fma((double)H[j], 268435456.0, (double)Lo[j]);   // H 2^28 + Lo
+                const double cv = ldexp(v, er + fs - MX_W * L);
+                const double x = X ? X[rr * MX_BS + sc] : 0.0;
+                const double out = a.mode == 2 ? 2.0 * x - cv : cv;
+                if (a.mode != 0) idem2 = fma(cv - x, cv - x, idem2);
+                fro2 = fma(out, out, fro2);
+                if (bi == jb && rr == sc) tr += out;
+                if (Co) Co[rr * MX_BS + sc] = out;
+                if (Ct) Ct[sc * MX_BS + rr] = out;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            fro2 += __shfl_xor_sync(0xffffffffu, fro2, o);
+            tr += __shfl_xor_sync(0xffffffffu, tr, o);
+            idem2 += __shfl_xor_sync(0xffffffffu, idem2, o);
+        }
+        if (lane == 0) {
+            red[ew * 3 + 0] = fro2;
+            red[ew * 3 + 1] = tr;
+            red[ew * 3 + 2] = idem2;
+        }
+    }
+    tc::fence_before();
+    __syncthreads();
+    if (tid < 2) {
+        // half h: epilogue warps whose quarter is 2h or 2h+1, in warp order
+        const int h = tid;
+        double f = 0.0, tr = 0.0, id = 0.0;
+        for (int ew = 0; ew < 16; ++ew) {
+            const int quarter = (ew + 2) & 3;
+            if ((quarter >> 1) != h) continue;
+            f += red[ew * 3 + 0];
+            tr += red[ew * 3 + 1];
+            id += red[ew * 3 + 2];
+        }
+        const int32_t ost = a.work_out[4 * w + 2 + h];
+        const double mult = ost >= 0 ? 2.0 : 1.0;
+        a.part_fro2[2 * w + h] = mult * f;
+        a.part_trace[2 * w + h] = tr;
+        a.part_idem2[2 * w + h] = mult * id;
+        const int nb = a.nb;
+        const int32_t ij = a.work_ij[w];
+        const int bi = 2 * (ij / nb) + h, jb = ij % nb;
+        const double nrm = sqrt(f);
+        if (a.work_out[4 * w + h] >= 0) a.normC[(int64_t)bi * nb + jb] = nrm;
+        if (ost >= 0) a.normC[(int64_t)jb * nb + bi] = nrm;
+        if (*s_err && h == 0) atomicExch(a.status, *s_err);
+    }
+    tc::fence_after();
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------- host side
+
+static uint8_t* g_zero_chunk[64] = {nullptr};
+
+static int zero_chunk(spamm_ctx* ctx, const uint8_t** out) {
+    if (!g_zero_chunk[ctx->device]) {
+        uint8_t* p = nullptr;
+        SP_CUDA(cudaMalloc(&p, CHUNK));
+        SP_CUDA(cudaMemset(p, 0, CHUNK));
+        g_zero_chunk[ctx->device] = p;
+    }
+    *out = g_zero_chunk[ctx->device];
+    return SPAMM_OK;
+}
+
+int mixed_available() { return 1; }
+
+int mixed_prepare(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, int sym,
+                  MixedPrep* mp) {
+    if (A->bs != MX_BS) {
+        set_error("mixed-precision leaf products need bs = 64");
+        return SPAMM_ENOTSUP;
+    }
+    SliceSet* sa = new SliceSet();
+    SliceSet* sb = sym ? sa : new SliceSet();
+    SP_TRY(split_matrix(ctx, A, 0, sa));
+    if (!sym) SP_TRY(split_matrix(ctx, B, 1, sb));
+    mp->sa = sa;
+    mp->sb = sb;
+    mp->sym = sym;
+    return SPAMM_OK;
+}
+
+void mixed_release(spamm_ctx* ctx, MixedPrep* mp) {
+    SliceSet* sa = (SliceSet*)mp->sa;
+    SliceSet* sb = (SliceSet*)mp->sb;
+    if (sa) sa->free(ctx->stream);
+    if (sb && sb != sa) {
+        sb->free(ctx->stream);
+        delete sb;
+    }
+    delete sa;
+    mp->sa = mp->sb = nullptr;
+}
+
+ChargeData mixed_charge(const spamm_mat* A, const spamm_mat* B, const double* nA,
+                        const double* nB, const MixedPrep& mp, int lmax) {
+    ChargeData ch;
+    const SliceSet* sa = (const SliceSet*)mp.sa;
+    const SliceSet* sb = (const SliceSet*)mp.sb;
+    ch.nb = A->nb;
+    ch.mapA = A->d_map;
+    ch.mapB = B->d_map;
+    ch.nA = nA;
+    ch.nB = nB;
+    ch.snA = sa->sn;
+    ch.tnA = sa->tn;
+    ch.snB = sb->sn;
+    ch.tnB = sb->tn;
+    ch.lmax = lmax;
+    ch.bt_from_a = mp.sym;
+    return ch;
+}
+
+int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
+                        const double* nB, const double* d_tau, const MixedPrep& mp, int lmax,
+                        int mode, int sym, spamm_mat** C_out, int64_t* n_cand, int64_t* n_kept,
+                        int64_t* n_formed, int64_t* n_pairs_out) {
+    cudaStream_t s = ctx->stream;
+    DevScalars* sc = (DevScalars*)ctx->d_scalars;
+    const int nb = A->nb;
+    const int64_t nb2 = (int64_t)nb * nb;
+    const SliceSet* sa = (const SliceSet*)mp.sa;
+    const SliceSet* sbs = (const SliceSet*)mp.sb;
+    ChargeData ch = mixed_charge(A, B, nA, nB, mp, lmax);
+    // block-level flags (kept under the mixed rule) -> output slots
+    int32_t *cnt = nullptr, *wf = nullptr, *of = nullptr;
+    int64_t *toff = nullptr, *widx = nullptr, *oidx = nullptr;
+    SP_TRY(dalloc((void**)&cnt, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&wf, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&of, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&toff, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&widx, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&oidx, sizeof(int64_t) * (nb2 + 1), s));
+    SP_CUDA(cudaMemsetAsync(&sc->n_cand, 0, 2 * sizeof(unsigned long long), s));
+    SP_TRY(plan_count_blocks(ctx, A, B, nA, nB, d_tau, mode ? A : nullptr, mode == 2, sym, &ch, cnt,
+                             wf, of));
+    SP_TRY(scan_i32_to_i64(ctx, of, oidx, nb2, &sc->n_out));
+    SP_TRY(scan_i32_to_i64(ctx, cnt, toff, nb2, &sc->n_tasks));   // formed products (blocks)
+    unsigned long long h[4];
+    SP_CUDA(cudaMemcpyAsync(h, &sc->n_cand, 16, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaMemcpyAsync(h + 2, &sc->n_out, 8, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaMemcpyAsync(h + 3, &sc->n_tasks, 8, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    *n_cand = (int64_t)h[0];
+    *n_kept = (int64_t)h[1];
+    *n_formed = (int64_t)h[3];
+    spamm_mat* C = nullptr;
+    SP_TRY(mat_alloc(ctx, A->n, A->bs, (int64_t)h[2], &C));
+    C->nslots = C->nnzb = (int64_t)h[2];
+    // map and coordinates of the output
+    SP_TRY(plan_write_out_map(ctx, of, oidx, nb, C));
+    // pair work items
+    const int np = (nb + 1) / 2;
+    const int64_t npb = (int64_t)np * nb;
+    int32_t *pc = nullptr, *pwf = nullptr;
+    int64_t *ptoff = nullptr, *pwidx = nullptr;
+    unsigned long long* d_tot = nullptr;
+    SP_TRY(dalloc((void**)&pc, sizeof(int32_t) * npb, s));
+    SP_TRY(dalloc((void**)&pwf, sizeof(int32_t) * npb, s));
+    SP_TRY(dalloc((void**)&ptoff, sizeof(int64_t) * (npb + 1), s));
+    SP_TRY(dalloc((void**)&pwidx, sizeof(int64_t) * (npb + 1), s));
+    SP_TRY(dalloc((void**)&d_tot, 16, s));
+    const unsigned G = (unsigned)((npb + 255) / 256);
+    ++ctx->launches;
+    k_pair_count<<<G, 256, 0, s>>>(ch, of, mode ? A->d_map : nullptr, sym, d_tau, pc, pwf);
+    SP_CHECK_LAUNCH();
+    SP_TRY(scan_i32_to_i64(ctx, pc, ptoff, npb, d_tot));
+    SP_TRY(scan_i32_to_i64(ctx, pwf, pwidx, npb, d_tot + 1));
+    unsigned long long hp[2];
+    SP_CUDA(cudaMemcpyAsync(hp, d_tot, 16, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_pt = (int64_t)hp[0], n_work = (int64_t)hp[1];
+    *n_pairs_out = n_pt;
+    int32_t *work_ij = nullptr, *work_out = nullptr, *task = nullptr;
+    int64_t* work_off = nullptr;
+    double* parts = nullptr;
+    const int64_t nw = n_work > 0 ? n_work : 1;
+    SP_TRY(dalloc((void**)&work_ij, sizeof(int32_t) * nw, s));
+    SP_TRY(dalloc((void**)&work_out, sizeof(int32_t) * 4 * nw, s));
+    SP_TRY(dalloc((void**)&work_off, sizeof(int64_t) * (nw + 1), s));
+    SP_TRY(dalloc((void**)&task, sizeof(int32_t) * 3 * (n_pt > 0 ? n_pt : 1), s));
+    SP_TRY(dalloc((void**)&parts, sizeof(double) * 6 * nw, s));
+    SP_CUDA(cudaMemsetAsync(&sc->mx_formed, 0, 2 * sizeof(unsigned long long), s));
+    ++ctx->launches;
+    k_pair_fill<<<G, 256, 0, s>>>(ch, of, oidx, sym, d_tau, pwf, pwidx, ptoff, work_ij, work_out,
+                                  work_off, task, sa->p0, sbs->p0, &sc->mx_formed);
+    ++ctx->launches;
+    k_last_off<<<1, 1, 0, s>>>(work_off, n_work, ptoff, npb);
+    SP_CHECK_LAUNCH();
+    int st = SPAMM_OK;
+    if (n_work > 0) {
+        MixedArgs ga;
+        memset(&ga, 0, sizeof ga);
+        ga.slA = sa->slices;
+        ga.slB = sbs->slices;
+        ga.p0A = sa->p0;
+        ga.p0B = sbs->p0;
+        ga.expA = sa->expo;
+        ga.expB = sbs->expo;
+        SP_TRY(zero_chunk(ctx, &ga.zero_chunk));
+        ga.task = task;
+        ga.work_ij = work_ij;
+        ga.work_out = work_out;
+        ga.work_off = work_off;
+        ga.nb = nb;
+        ga.lmax = lmax;
+        // exact window: per product, a level sum is below 2^18 (L + 1) (2^20 for L = 2)
+        const double per = ldexp(1.0, 18) * (lmax + 1 > 4 ? lmax + 1 : 4);
+        ga.window = (int)floor((ldexp(1.0, 24) - 1.0) / per);
+        ga.mode = mode;
+        ga.mapX = mode ? A->d_map : nullptr;
+        ga.tilesX = mode ? A->d_tiles : nullptr;
+        ga.tilesC = C->d_tiles;
+        ga.normC = C->d_norm;
+        ga.part_fro2 = parts;
+        ga.part_trace = parts + 2 * nw;
+        ga.part_idem2 = parts + 4 * nw;
+        ga.status = &sc->status;
+        static bool attr_set[64] = {false};
+        if (!attr_set[ctx->device]) {
+            SP_CUDA(cudaFuncSetAttribute(k_gemm_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         GM_SMEM));
+            attr_set[ctx->device] = true;
+        }
+        SP_CUDA(cudaMemsetAsync(&sc->status, 0, sizeof(int32_t), s));
+        ++ctx->launches;
+        k_gemm_mixed<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(ga);
+        SP_CHECK_LAUNCH();
+        st = reduce_partials(ctx, parts, parts + 2 * nw, parts + 4 * nw, 2 * n_work);
+    } else {
+        SP_CUDA(cudaMemsetAsync(&sc->fro2, 0, 3 * sizeof(double), s));
+    }
+    dfree(cnt, s); dfree(wf, s); dfree(of, s); dfree(toff, s); dfree(widx, s); dfree(oidx, s);
+    dfree(pc, s); dfree(pwf, s); dfree(ptoff, s); dfree(pwidx, s); dfree(d_tot, s);
+    dfree(work_ij, s); dfree(work_out, s); dfree(work_off, s); dfree(task, s); dfree(parts, s);
+    if (st != SPAMM_OK) {
+        spamm_mat_free(C);
+        return st;
+    }
+    *C_out = C;
+    return SPAMM_OK;
+}
+
+}  // namespace spamm

@@ -12,19 +12,25 @@
 // One thread per output block walks k = 0..nb-1 over the two dense block maps;
 // three exclusive scans give work-item, output-slot and task offsets; a second
 // walk writes the (slot of A_ik, slot of B_kj) pairs.
+//
+// Symmetric mode (SP2 steps, A = B = X = X^T with a bitwise-symmetric norm map):
+// the kept set of block (j, i) is the transpose of that of (i, j), because
+// p_jki = n_jk n_ki = n_kj n_ik = p_ikj exactly. Only blocks i <= j become work
+// items; the leaf-product kernel writes C_ij and C_ji = C_ij^T.
 #include "common.cuh"
 
 namespace spamm {
 
 __global__ void k_plan_count(const int32_t* __restrict__ mapA, const double* __restrict__ nA,
                              const int32_t* __restrict__ mapB, const double* __restrict__ nB,
-                             const int32_t* __restrict__ mapX, int nb, int mode_dbl,
-                             const double* __restrict__ d_tau, int32_t* __restrict__ cnt,
+                             const int32_t* __restrict__ mapX, int nb, int mode_dbl, int sym,
+                             ChargeData ch, const double* __restrict__ d_tau,
+                             int32_t* __restrict__ cnt,
                              int32_t* __restrict__ work_flag, int32_t* __restrict__ out_flag,
                              unsigned long long* __restrict__ n_cand) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nb2 = (int64_t)nb * nb;
-    unsigned long long cand = 0;
+    unsigned long long cand = 0, kept_full = 0;
     if (b < nb2) {
         const int i = (int)(b / nb), j = (int)(b % nb);
         const double tau = *d_tau;
@@ -35,43 +41,60 @@ __global__ void k_plan_count(const int32_t* __restrict__ mapA, const double* __r
             if (sa < 0 || sb < 0) continue;
             ++cand;
             const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
-            if (!(p < tau)) ++kept;
+            if (p < tau) continue;
+            // mixed rule: a product is formed only when its charge is below its norm product
+            if (ch.lmax > 0 &&
+                !(charge(ch, sa, charge_bslot(ch, k, j), nB[(int64_t)k * nb + j]) < p))
+                continue;
+            ++kept;
         }
         const int hx = mapX ? (mapX[b] >= 0) : 0;
-        cnt[b] = kept;
         const int of = kept > 0 || (mode_dbl && hx);
+        const int lower = sym && i > j;     // produced by the mirror work item
+        cnt[b] = lower ? 0 : kept;
         out_flag[b] = of;
-        work_flag[b] = of || hx;
+        work_flag[b] = lower ? 0 : (of || hx);
+        kept_full = kept;
     }
     // warp-aggregated candidate count
-    for (int o = 16; o > 0; o >>= 1) cand += __shfl_xor_sync(0xffffffffu, cand, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        cand += __shfl_xor_sync(0xffffffffu, cand, o);
+        kept_full += __shfl_xor_sync(0xffffffffu, kept_full, o);
+    }
     if ((threadIdx.x & 31) == 0 && cand) atomicAdd(n_cand, cand);
+    if ((threadIdx.x & 31) == 0 && kept_full) atomicAdd(n_cand + 1, kept_full);
 }
 
 __global__ void k_plan_fill(const int32_t* __restrict__ mapA, const double* __restrict__ nA,
                             const int32_t* __restrict__ mapB, const double* __restrict__ nB,
-                            int nb, const double* __restrict__ d_tau,
+                            int nb, int sym, const double* __restrict__ d_tau,
                             const int32_t* __restrict__ cnt, const int32_t* __restrict__ work_flag,
                             const int32_t* __restrict__ out_flag,
                             const int64_t* __restrict__ task_off, const int64_t* __restrict__ work_idx,
                             const int64_t* __restrict__ out_idx, int32_t* __restrict__ work_ij,
-                            int32_t* __restrict__ work_out, int64_t* __restrict__ work_off,
+                            int32_t* __restrict__ work_out, int32_t* __restrict__ work_out_t,
+                            int64_t* __restrict__ work_off,
                             int32_t* __restrict__ task_a, int32_t* __restrict__ task_b,
                             int32_t* __restrict__ mapC, int32_t* __restrict__ coordC) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nb2 = (int64_t)nb * nb;
-    if (b >= nb2 || !work_flag[b]) return;
-    const int i = (int)(b / nb), j = (int)(b % nb);
-    const int64_t w = work_idx[b];
-    const int64_t off = task_off[b];
+    if (b >= nb2) return;
     const int32_t os = out_flag[b] ? (int32_t)out_idx[b] : -1;
-    work_ij[w] = (int32_t)b;
-    work_out[w] = os;
-    work_off[w] = off;
     if (os >= 0) {
         mapC[b] = os;
         coordC[os] = (int32_t)b;
     }
+    if (!work_flag[b]) return;
+    const int i = (int)(b / nb), j = (int)(b % nb);
+    const int64_t w = work_idx[b];
+    const int64_t off = task_off[b];
+    work_ij[w] = (int32_t)b;
+    work_out[w] = os;
+    if (work_out_t) {
+        const int64_t bt = (int64_t)j * nb + i;
+        work_out_t[w] = (sym && i != j && out_flag[bt]) ? (int32_t)out_idx[bt] : -1;
+    }
+    work_off[w] = off;
     if (cnt[b] == 0) return;
     const double tau = *d_tau;
     int64_t t = off;
@@ -88,6 +111,40 @@ __global__ void k_plan_fill(const int32_t* __restrict__ mapA, const double* __re
     }
 }
 
+__global__ void k_write_out_map(const int32_t* __restrict__ of, const int64_t* __restrict__ oidx,
+                                int64_t nb2, int32_t* __restrict__ mapC,
+                                int32_t* __restrict__ coordC) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb2 || !of[b]) return;
+    mapC[b] = (int32_t)oidx[b];
+    coordC[oidx[b]] = (int32_t)b;
+}
+
+int plan_count_blocks(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
+                      const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
+                      int sym, const ChargeData* ch, int32_t* cnt, int32_t* wf, int32_t* of) {
+    DevScalars* sc = (DevScalars*)ctx->d_scalars;
+    const int nb = A->nb;
+    const int64_t nb2 = (int64_t)nb * nb;
+    const unsigned G = (unsigned)((nb2 + 255) / 256);
+    ++ctx->launches;
+    k_plan_count<<<G, 256, 0, ctx->stream>>>(A->d_map, nA, B->d_map, nB, X ? X->d_map : nullptr,
+                                             nb, mode_dbl, sym, ch ? *ch : ChargeData(), d_tau,
+                                             cnt, wf, of, &sc->n_cand);
+    SP_CHECK_LAUNCH();
+    return SPAMM_OK;
+}
+
+int plan_write_out_map(spamm_ctx* ctx, const int32_t* of, const int64_t* oidx, int nb,
+                       spamm_mat* C) {
+    const int64_t nb2 = (int64_t)nb * nb;
+    ++ctx->launches;
+    k_write_out_map<<<(unsigned)((nb2 + 255) / 256), 256, 0, ctx->stream>>>(of, oidx, nb2, C->d_map,
+                                                                           C->d_coord);
+    SP_CHECK_LAUNCH();
+    return SPAMM_OK;
+}
+
 __global__ void k_plan_last_off(int64_t* work_off, int64_t n_work, const int64_t* task_off,
                                 int64_t nb2) {
     work_off[n_work] = task_off[nb2];
@@ -96,6 +153,7 @@ __global__ void k_plan_last_off(int64_t* work_off, int64_t n_work, const int64_t
 void plan_free(Plan* p, cudaStream_t s) {
     dfree(p->d_work_ij, s);
     dfree(p->d_work_out, s);
+    dfree(p->d_work_out_t, s);
     dfree(p->d_work_off, s);
     dfree(p->d_task_a, s);
     dfree(p->d_task_b, s);
@@ -106,8 +164,9 @@ void plan_free(Plan* p, cudaStream_t s) {
 // Builds the plan and the output matrix's block map (C must be allocated by the
 // caller afterwards with cap = plan->n_out; the map is written into *mapC_out
 // which the caller adopts).
-int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* d_tau,
-                    const spamm_mat* X, int mode_dbl, Plan* plan, spamm_mat** C_out) {
+int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
+                    const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
+                    int sym, Plan* plan, spamm_mat** C_out) {
     cudaStream_t s = ctx->stream;
     DevScalars* sc = (DevScalars*)ctx->d_scalars;
     const int nb = A->nb;
@@ -122,12 +181,10 @@ int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, cons
     SP_TRY(dalloc((void**)&toff, sizeof(int64_t) * (nb2 + 1), s));
     SP_TRY(dalloc((void**)&widx, sizeof(int64_t) * (nb2 + 1), s));
     SP_TRY(dalloc((void**)&oidx, sizeof(int64_t) * (nb2 + 1), s));
-    SP_CUDA(cudaMemsetAsync(&sc->n_cand, 0, sizeof(unsigned long long), s));
+    SP_CUDA(cudaMemsetAsync(&sc->n_cand, 0, 2 * sizeof(unsigned long long), s));
     const int T = 256;
     const unsigned G = (unsigned)((nb2 + T - 1) / T);
-    k_plan_count<<<G, T, 0, s>>>(A->d_map, A->d_norm, B->d_map, B->d_norm, X ? X->d_map : nullptr,
-                                 nb, mode_dbl, d_tau, cnt, wf, of, &sc->n_cand);
-    SP_CHECK_LAUNCH();
+    SP_TRY(plan_count_blocks(ctx, A, B, nA, nB, d_tau, X, mode_dbl, sym, nullptr, cnt, wf, of));
     SP_TRY(scan_i32_to_i64(ctx, cnt, toff, nb2, &sc->n_tasks));
     unsigned long long* d_nwork = nullptr;
     SP_TRY(dalloc((void**)&d_nwork, sizeof(unsigned long long), s));
@@ -137,26 +194,31 @@ int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, cons
     SP_CUDA(cudaMemcpyAsync(&h[0], &sc->n_tasks, 8, cudaMemcpyDeviceToHost, s));
     SP_CUDA(cudaMemcpyAsync(&h[1], d_nwork, 8, cudaMemcpyDeviceToHost, s));
     SP_CUDA(cudaMemcpyAsync(&h[2], &sc->n_out, 8, cudaMemcpyDeviceToHost, s));
-    unsigned long long hc = 0;
-    SP_CUDA(cudaMemcpyAsync(&hc, &sc->n_cand, 8, cudaMemcpyDeviceToHost, s));
+    unsigned long long hc[2] = {0, 0};
+    SP_CUDA(cudaMemcpyAsync(hc, &sc->n_cand, 16, cudaMemcpyDeviceToHost, s));
     SP_CUDA(cudaStreamSynchronize(s));
     plan->n_tasks = (int64_t)h[0];
     plan->n_work = (int64_t)h[1];
     plan->n_out = (int64_t)h[2];
-    plan->n_cand = (int64_t)hc;
+    plan->n_cand = (int64_t)hc[0];
+    plan->n_kept_full = (int64_t)hc[1];
     spamm_mat* C = nullptr;
     SP_TRY(mat_alloc(ctx, A->n, A->bs, plan->n_out, &C));
     C->nslots = plan->n_out;
     C->nnzb = plan->n_out;
     SP_TRY(dalloc((void**)&plan->d_work_ij, sizeof(int32_t) * (plan->n_work + 1), s));
     SP_TRY(dalloc((void**)&plan->d_work_out, sizeof(int32_t) * (plan->n_work + 1), s));
+    if (sym) SP_TRY(dalloc((void**)&plan->d_work_out_t, sizeof(int32_t) * (plan->n_work + 1), s));
+    plan->sym = sym;
     SP_TRY(dalloc((void**)&plan->d_work_off, sizeof(int64_t) * (plan->n_work + 1), s));
     SP_TRY(dalloc((void**)&plan->d_task_a, sizeof(int32_t) * (plan->n_tasks + 1), s));
     SP_TRY(dalloc((void**)&plan->d_task_b, sizeof(int32_t) * (plan->n_tasks + 1), s));
-    k_plan_fill<<<G, T, 0, s>>>(A->d_map, A->d_norm, B->d_map, B->d_norm, nb, d_tau, cnt, wf, of,
+    ++ctx->launches;
+    k_plan_fill<<<G, T, 0, s>>>(A->d_map, nA, B->d_map, nB, nb, sym, d_tau, cnt, wf, of,
                                 toff, widx, oidx, plan->d_work_ij, plan->d_work_out,
-                                plan->d_work_off, plan->d_task_a, plan->d_task_b, C->d_map,
+                                plan->d_work_out_t, plan->d_work_off, plan->d_task_a, plan->d_task_b, C->d_map,
                                 C->d_coord);
+    ++ctx->launches;
     k_plan_last_off<<<1, 1, 0, s>>>(plan->d_work_off, plan->n_work, toff, nb2);
     SP_CHECK_LAUNCH();
     dfree(cnt, s);

@@ -254,11 +254,14 @@ int truncate_blocks(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric, i
     unsigned long long* keys = nullptr;
     SP_TRY(dalloc((void**)&keys, sizeof(unsigned long long) * nb2, s));
     const double delta2 = delta * delta;
+    ++ctx->launches;
     k_trunc_keys<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(X->d_map, X->d_norm, nb, symmetric,
                                                                delta2, keys);
+    ++ctx->launches;
     k_trunc_select<<<1, 1024, 0, s>>>(keys, nb2, nb, symmetric, X->d_map, X->d_norm, X->d_coord,
                                       sc);
     SP_CUDA(cudaMemsetAsync(&sc->n_out, 0, sizeof(unsigned long long), s));
+    ++ctx->launches;
     k_count_live<<<64, 256, 0, s>>>(X->d_map, nb2, &sc->n_out);
     SP_CHECK_LAUNCH();
     unsigned long long h_rem = 0, h_live = 0;

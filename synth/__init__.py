@@ -65,12 +65,20 @@ class FockProblem:
     lumo: float          # lower bound on the (n_occ+1)-th smallest eigenvalue
     decay: float
     gap_mode: str
+    occupied: np.ndarray = None   # occupied eigenvectors (gap_mode="eig", keep_vectors=True)
+    eigvals: np.ndarray = None    # spectrum of F after the shift (gap_mode="eig")
 
 
 def lattice_fock(n: int, seed: int = SEED_BASE, decay: float = 0.8,
                  gap: float = 0.1, gap_mode: str = "eig", jitter: float = 0.1,
-                 funcs_per_site: int = 4, drop: float = 0.0) -> FockProblem:
-    """Fock-like matrix on a jittered cubic lattice (basis in Morton order of sites)."""
+                 funcs_per_site: int = 4, drop: float = 0.0, eigh=None,
+                 keep_vectors: bool = False) -> FockProblem:
+    """Fock-like matrix on a jittered cubic lattice (basis in Morton order of sites).
+
+    ``eigh`` (optional) replaces numpy.linalg.eigh for the eigenvector-based
+    gap shift, e.g. a GPU eigensolver for large n; it must return ascending
+    eigenvalues and orthonormal eigenvectors as numpy arrays.
+    """
     if n % funcs_per_site:
         raise ValueError("n must be a multiple of funcs_per_site")
     g = rng(seed)
@@ -78,31 +86,46 @@ def lattice_fock(n: int, seed: int = SEED_BASE, decay: float = 0.8,
     pts = _morton_points(sites).astype(np.float64)
     pts = pts + g.uniform(-jitter, jitter, size=pts.shape)
     centre = np.repeat(pts, funcs_per_site, axis=0)
-    diff = centre[:, None, :] - centre[None, :, :]
-    d = np.sqrt(np.einsum("ijk,ijk->ij", diff, diff))
-    del diff
+    F = np.zeros((n, n))
+    for ax in range(3):                      # squared distances, one axis at a time
+        c = centre[:, ax]
+        dif = c[:, None] - c[None, :]
+        dif *= dif
+        F += dif
+        del dif
+    np.sqrt(F, out=F)
+    F *= -decay
+    np.exp(F, out=F)
     noise = g.standard_normal(size=(n, n))
-    F = -np.exp(-decay * d) * (1.0 + 0.1 * noise)
-    del noise, d
-    F = 0.5 * (F + F.T)
+    noise *= 0.1
+    noise += 1.0
+    F *= noise
+    F *= -1.0
+    del noise
+    F += F.T.copy()
+    F *= 0.5
     np.fill_diagonal(F, g.uniform(-0.5, 0.5, size=n))
     if drop > 0:
         F[np.abs(F) < drop] = 0.0
     n_occ = n // 2
+    vo = None
     if gap_mode == "eig":
-        w, v = np.linalg.eigh(F)
+        w, v = (eigh or np.linalg.eigh)(F)
         natural = w[n_occ] - w[n_occ - 1]
         s = max(0.0, gap - natural)
+        vo = v[:, :n_occ]
         if s > 0.0:
-            vo = v[:, :n_occ]
-            F = F + s * (np.eye(n) - vo @ vo.T)
-            F = 0.5 * (F + F.T)
+            F += s * np.eye(n)
+            F -= s * (vo @ vo.T)
+            F += F.T.copy()
+            F *= 0.5
         homo = float(w[n_occ - 1])
         lumo = float(w[n_occ] + s)
         # eigenvector roundoff moves eigenvalues by ~1e-13 * |F|; keep the bounds safe
         slack = 1e-9 * float(np.abs(w).max())
         homo += slack
         lumo -= slack
+        del v
     elif gap_mode == "stagger":
         # functions 0,1 of each site go down by s, functions 2,3 go up by s;
         # Gershgorin discs of the two groups are then disjoint with a gap >= gap.
@@ -114,7 +137,12 @@ def lattice_fock(n: int, seed: int = SEED_BASE, decay: float = 0.8,
         lumo = -0.5 + s - R
     else:
         raise ValueError(gap_mode)
-    return FockProblem(np.ascontiguousarray(F), n_occ, homo, lumo, decay, gap_mode)
+    P = FockProblem(np.ascontiguousarray(F), n_occ, homo, lumo, decay, gap_mode)
+    if gap_mode == "eig":
+        P.eigvals = np.concatenate([w[:n_occ], w[n_occ:] + s])
+    if keep_vectors:
+        P.occupied = vo
+    return P
 
 
 def random_decaying(n: int, seed: int, length: float = 6.0, symmetric: bool = False,

@@ -205,9 +205,16 @@ def test_sp2_step_matches_oracle(gctx, orc, branch):
     G = gctx.from_dense(X, 64)
     tau = 1e-9
     Xn, rep = gctx.sp2_step(G, branch, tau=tau)
-    C, _ = orc.spamm(X, X, tau, 64)
+    C, cnt = orc.spamm(X, X, tau, 64)
     want = C if branch == 0 else 2 * X - C
-    assert _rel(Xn.to_numpy(), want) <= REL
+    got = Xn.to_numpy()
+    assert _rel(got, want) <= REL
+    # symmetric X: only blocks i <= j are formed and mirrored, so the result is exactly symmetric
+    np.testing.assert_array_equal(got, got.T)
+    kept, border, _ = _flat_kept(orc, X, X, tau, 64)
+    assert cnt == kept and abs(rep["kept"] - kept) <= border
+    nb = 512 // 64
+    assert rep["formed"] < rep["kept"] and rep["formed"] >= rep["kept"] // 2
     assert rep["idem"] == pytest.approx(np.linalg.norm(C - X), rel=1e-10)
     assert rep["trace_out"] == pytest.approx(np.trace(want), rel=1e-12)
 
