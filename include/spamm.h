@@ -160,6 +160,30 @@ int spamm_sp2_step(spamm_ctx* ctx, const spamm_mat* X, int branch, double delta,
 int spamm_truncate(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric,
                    spamm_report* rep);
 
+/* Allocation-free tau search. The paper has no counterpart: this exists for
+   callers that cannot call cudaMalloc -- code that runs where allocation is not
+   allowed or not wanted, such as a host thread that must not synchronise the
+   device, or a host that manages all device memory itself -- and so cannot
+   create a spamm_ctx or spamm_mat (both allocate).
+   Inputs: d_norm_a, d_norm_b are device arrays of nb*nb float64 leaf-block
+   Frobenius norms of A and B, row-major (entry i*nb + k is ||A_ik||_F; 0 for an
+   absent block). Outputs (device pointers, each may be NULL): *d_index = the
+   0-based index of the chosen candidate (-1: none, exact product), *d_tau =
+   that tau (0 for none), *d_bound = its Algorithm 3 bound. The search is the
+   one spamm_multiply runs (same kernels, same result), ordered on cuda_stream
+   (a cudaStream_t, NULL for the default stream); the call returns without
+   waiting for it.
+   Scratch: one fixed device array of about 516 KB that every device loading the
+   library holds until exit; nb > 256 is rejected with SPAMM_EINVAL. Nothing is
+   allocated. The first call on each device resolves that array's address and
+   writes the tau table into it, so make that first call before any stream
+   capture. Every call shares the array: calls that overlap on the GPU (on
+   different streams, or from several threads) race and must be serialised by
+   the caller. */
+int spamm_cse_search_noalloc(const double* d_norm_a, const double* d_norm_b, int64_t nb,
+                             double delta, int32_t* d_index, double* d_tau, double* d_bound,
+                             void* cuda_stream);
+
 /* ------------------------------------------------------------ purification */
 
 typedef struct {

@@ -101,6 +101,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_sp2_step": ([vp, vp, i32, d, d, i32, P(vp), P(Report)], i32),
         "spamm_truncate": ([vp, vp, d, i32, P(Report)], i32),
         "spamm_purify": ([vp, vp, i64, d, i32, P(PurifyOpts), P(vp), P(PurifyReport)], i32),
+        "spamm_cse_search_noalloc": ([vp, vp, i64, d, vp, vp, vp, vp], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

@@ -262,3 +262,53 @@ extern "C" int spamm_cse(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B,
     dfree(d, s);
     return SPAMM_OK;
 }
+
+namespace spamm {
+
+// Tau search over raw norm maps with every buffer supplied by the caller (used
+// by the allocation-free entry point): the same kernels and the same order of
+// operations as cse_search, launched on stream s, allocating nothing.
+int cse_search_scratch(cudaStream_t s, const double* nA, const double* nB, int nb, double delta,
+                       const double* d_tau_table, DevScalars* sc, double* buf0, double* buf1) {
+    int NB = 1;
+    while (NB < nb) NB <<= 1;
+    int L0 = 0;
+    while ((1 << L0) < NB) ++L0;
+    const int N = SPAMM_N_TAU;
+    int steps = 0;
+    while ((1 << steps) < N + 1) ++steps;
+    k_bisect_init<<<1, 1, 0, s>>>(sc, d_tau_table, N);
+    for (int it = 0; it < steps; ++it) {
+        if (L0 == 0) {
+            k_cse_cube<true><<<1, 1, 0, s>>>(nA, nB, nb, nullptr, 1, &sc->tau_mid, ChargeData(),
+                                             &sc->done, 0, &sc->err_mid);
+        } else {
+            int L = L0, side = NB;
+            int lv = L < 3 ? L : 3;
+            int out_side = side >> lv;
+            double* out = (out_side == 1) ? &sc->err_mid : buf0;
+            k_cse_cube<true><<<out_side * out_side * out_side, 1 << (3 * lv), 0, s>>>(
+                nA, nB, nb, nullptr, side, &sc->tau_mid, ChargeData(), &sc->done, lv, out);
+            L -= lv;
+            side = out_side;
+            double* in = buf0;
+            double* other = buf1;
+            while (L > 0) {
+                lv = L < 3 ? L : 3;
+                out_side = side >> lv;
+                out = (out_side == 1) ? &sc->err_mid : other;
+                k_cse_cube<false><<<out_side * out_side * out_side, 1 << (3 * lv), 0, s>>>(
+                    nullptr, nullptr, nb, in, side, &sc->tau_mid, ChargeData(), &sc->done, lv, out);
+                L -= lv;
+                side = out_side;
+                double* tmp = in;
+                in = other;
+                other = tmp;
+            }
+        }
+        k_bisect_step<<<1, 1, 0, s>>>(sc, d_tau_table, delta);
+    }
+    return cudaGetLastError() == cudaSuccess ? SPAMM_OK : SPAMM_ECUDA;
+}
+
+}  // namespace spamm
