@@ -214,6 +214,8 @@ typedef struct {
     double* step_idem;
     int32_t* step_branch;    /* 0: X^2, 1: 2X - X^2 */
     int64_t* step_nnzb;
+    int32_t* step_lmax;      /* slice levels of the step's product (0: float64 leaf products) */
+    float* step_ms;          /* wall time of each step (CUDA events) */
 } spamm_purify_report;
 
 /* SP2 purification of F (symmetric) with error control so that

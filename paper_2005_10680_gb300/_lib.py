@@ -58,7 +58,8 @@ class PurifyReport(ctypes.Structure):
                 ("cand_total", ctypes.c_int64),
                 ("ms_total", ctypes.c_double), ("ms_phase", ctypes.c_double * 8),
                 ("step_delta", _PD), ("step_tau", _PD), ("step_trace", _PD),
-                ("step_idem", _PD), ("step_branch", _PI32), ("step_nnzb", _PI64)]
+                ("step_idem", _PD), ("step_branch", _PI32), ("step_nnzb", _PI64),
+                ("step_lmax", _PI32), ("step_ms", ctypes.POINTER(ctypes.c_float))]
 
 
 _lib = None
@@ -311,6 +312,8 @@ class Context:
         logs = {k: np.zeros(n_iter) for k in ("delta", "tau", "trace", "idem")}
         br = np.zeros(n_iter, dtype=np.int32)
         nz = np.zeros(n_iter, dtype=np.int64)
+        lm = np.zeros(n_iter, dtype=np.int32)
+        sms = np.zeros(n_iter, dtype=np.float32)
         rep = PurifyReport()
         rep.step_delta = logs["delta"].ctypes.data_as(_PD)
         rep.step_tau = logs["tau"].ctypes.data_as(_PD)
@@ -318,6 +321,8 @@ class Context:
         rep.step_idem = logs["idem"].ctypes.data_as(_PD)
         rep.step_branch = br.ctypes.data_as(_PI32)
         rep.step_nnzb = nz.ctypes.data_as(_PI64)
+        rep.step_lmax = lm.ctypes.data_as(_PI32)
+        rep.step_ms = sms.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         out = ctypes.c_void_p()
         st = _lib.spamm_purify(self.handle, F.handle, int(n_occ), float(eps), int(n_iter),
                                ctypes.byref(opts), ctypes.byref(out), ctypes.byref(rep))
@@ -330,5 +335,6 @@ class Context:
              "ms_phase": list(rep.ms_phase), "status": st,
              "deltas": logs["delta"][:it].tolist(), "taus": logs["tau"][:it].tolist(),
              "traces": logs["trace"][:it].tolist(), "idems": logs["idem"][:it].tolist(),
-             "branches": br[:it].tolist(), "nnzb": nz[:it].tolist()}
+             "branches": br[:it].tolist(), "nnzb": nz[:it].tolist(),
+             "lmax": lm[:it].tolist(), "step_ms": sms[:it].tolist()}
         return Matrix(self, out.value), r

@@ -11,7 +11,6 @@ using namespace spamm;
 
 namespace {
 
-enum { EV_T0 = 0, EV_CSE0, EV_CSE1, EV_PLAN1, EV_GEMM1, EV_END, EV_TR0, EV_TR1 };
 
 __global__ void k_select_tau(DevScalars* sc, const double* __restrict__ tau, int N) {
     sc->tau_sel = sc->hi < N ? tau[sc->hi] : 0.0;
@@ -126,10 +125,9 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     double* parts = nullptr;
     if (st == SPAMM_OK && use_mixed) {
         int64_t npairs = 0;
+        // records EV_PLAN1 before and EV_GEMM1 after the leaf-product kernel
         st = mixed_plan_and_gemm(ctx, A, B, nA, nB, &sc->tau_sel, mp, lmax_used, mode, sym, &C,
                                  &n_cand, &n_kept, &n_tasks, &npairs);
-        cudaEventRecord(ctx->ev[EV_PLAN1], s);
-        cudaEventRecord(ctx->ev[EV_GEMM1], s);
         mixed_release(ctx, &mp);
     } else if (st == SPAMM_OK) {
         Plan plan;
@@ -567,6 +565,7 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
             R.converged = 1;
             break;
         }
+        float trunc_ms = 0.f;
         if (variant == SPAMM_TRUNCMUL || variant == SPAMM_HYBRID) {
             spamm_report tr;
             st = spamm_truncate(ctx, Xn, variant == SPAMM_TRUNCMUL ? delta : 0.5 * delta, 1, &tr);
@@ -575,6 +574,7 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
                 break;
             }
             R.ms_phase[SPAMM_T_TRUNC] += tr.ms[SPAMM_T_TRUNC];
+            trunc_ms = tr.ms[SPAMM_T_TRUNC];
             trace = tr.trace_out;
         } else {
             trace = mr.trace_out;
@@ -588,6 +588,8 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
         if (R.step_idem) R.step_idem[k] = idem;
         if (R.step_branch) R.step_branch[k] = sq ? 0 : 1;
         if (R.step_nnzb) R.step_nnzb[k] = Xn->nnzb;
+        if (R.step_lmax) R.step_lmax[k] = mr.lmax;
+        if (R.step_ms) R.step_ms[k] = mr.ms[SPAMM_T_TOTAL] + trunc_ms;
         R.iters = it;
         spamm_mat_free(X);
         X = Xn;

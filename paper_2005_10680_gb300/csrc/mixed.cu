@@ -767,12 +767,16 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
             attr_set[ctx->device] = true;
         }
         SP_CUDA(cudaMemsetAsync(&sc->status, 0, sizeof(int32_t), s));
+        cudaEventRecord(ctx->ev[EV_PLAN1], s);
         ++ctx->launches;
         k_gemm_mixed<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(ga);
         SP_CHECK_LAUNCH();
+        cudaEventRecord(ctx->ev[EV_GEMM1], s);
         st = reduce_partials(ctx, parts, parts + 2 * nw, parts + 4 * nw, 2 * n_work);
     } else {
+        cudaEventRecord(ctx->ev[EV_PLAN1], s);
         SP_CUDA(cudaMemsetAsync(&sc->fro2, 0, 3 * sizeof(double), s));
+        cudaEventRecord(ctx->ev[EV_GEMM1], s);
     }
     dfree(cnt, s); dfree(wf, s); dfree(of, s); dfree(toff, s); dfree(widx, s); dfree(oidx, s);
     dfree(pc, s); dfree(pwf, s); dfree(ptoff, s); dfree(pwidx, s); dfree(d_tot, s);
