@@ -81,10 +81,10 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         }
         cudaEventRecord(ctx->ev[EV_CSE0], s);
         // fewest levels whose certified charge (everything kept, tau = 0) stays within
-        // half of delta; with a given tau all 9 levels are formed
+        // half of delta; with a given tau every level up to 10 is formed
         lmax_used = 0;
-        const int first = search ? 4 : 9;
-        for (int L = first; L <= 9 && st == SPAMM_OK; ++L) {
+        const int first = search ? 4 : 10;
+        for (int L = first; L <= 10 && st == SPAMM_OK; ++L) {
             ChargeData ch = mixed_charge(A, B, nA, nB, mp, L);
             ++ctx->launches;
             k_set_tau<<<1, 1, 0, s>>>(sc, 0.0);

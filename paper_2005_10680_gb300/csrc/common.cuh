@@ -112,10 +112,12 @@ int scan_i32_to_i64(spamm_ctx* ctx, const int32_t* d_in, int64_t* d_out, int64_t
                     unsigned long long* d_total);
 
 // Charge of the mixed-precision leaf products (see mixed.cu): per stored block,
-// slice norms sn[p] = ||X_p||_F and tail norms tn[p] = ||X - sum_{q<=p} X_q||_F,
-// p = 1..8. A product formed from the level pairs p + q <= lmax has error at most
+// slice norms sn[p] = ||X_p||_F and tail norms tn[p] >= ||X - sum_{q<=p} X_q||_F,
+// p = 1..MX_SLICES. A product formed from the level pairs p + q <= lmax has error at most
 //   sum_{p=1}^{lmax-1} snA[p] tnB[lmax-p] + tnA[lmax-1] ||B_kj||_F.
 // lmax = 0 means "no charge" (float64 leaf products).
+constexpr int MX_SLICES = 9;      // digit slices per block in the mixed form
+
 struct ChargeData {
     int nb = 0;
     int lmax = 0;
@@ -133,9 +135,9 @@ struct ChargeData {
 __device__ __forceinline__ double charge(const ChargeData& ch, int32_t sa, int32_t sb,
                                          double norm_b) {
     const int L = ch.lmax;
-    const double* snA = ch.snA + (int64_t)sa * 8;
-    const double* tnA = ch.tnA + (int64_t)sa * 8;
-    const double* tnB = ch.tnB + (int64_t)sb * 8;
+    const double* snA = ch.snA + (int64_t)sa * MX_SLICES;
+    const double* tnA = ch.tnA + (int64_t)sa * MX_SLICES;
+    const double* tnB = ch.tnB + (int64_t)sb * MX_SLICES;
     double c = tnA[L - 2] * norm_b;
     for (int p = 1; p <= L - 1; ++p) c = fma(snA[p - 1], tnB[L - p - 1], c);
     return c;

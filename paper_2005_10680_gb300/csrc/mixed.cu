@@ -38,8 +38,8 @@
 namespace spamm {
 
 constexpr int MX_W = 7;
-constexpr int MX_S = 8;
-constexpr int MX_LMAX = 9;
+constexpr int MX_S = MX_SLICES;
+constexpr int MX_LMAX = 10;
 constexpr int MX_BS = 64;
 constexpr int CHUNK = 2048;                      // 64 rows x 16 K x 2 bytes
 constexpr int SLICE_BYTES = 4 * CHUNK;           // one slice of one 64 x 64 block
@@ -92,7 +92,15 @@ __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __re
 }
 
 // One CTA (256 threads) per stored block: digits, leading-zero slice, slice and
-// tail norms. transpose: slice the transposed block with column exponents.
+// tail norms, in integer arithmetic. With |x| < 2^e_r, V = x 2^(63 - e_r) is
+// rounded to an int64 (the rounding is the last tail, at most half a unit) and
+// cut from the bottom into balanced base-128 digits:
+//     d = ((V + 64) mod 128) - 64 in [-64, 63], V <- (V - d) / 128, ..., d_1 = V,
+// so x = sum_p d_p 2^(e_r - 7p) + T_9 with |d_1| <= 128, |T_9| <= 2^(e_r - 64).
+// Slice norms are exact (digit squares summed exactly per row in f32); tail norms
+// are upper bounds: (|R_p| + 1/2) per entry, summed in f32 and inflated by 2^-12
+// to cover the f32 rounding. transpose: slice the transposed block with column
+// exponents.
 __global__ void __launch_bounds__(256)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
         const int32_t* __restrict__ expo, uint8_t* __restrict__ slices, int8_t* __restrict__ p0,
@@ -113,49 +121,75 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
     __syncthreads();
     if (cd < 0) return;
     const int bi = cd / nb, bj = cd % nb;
-    // the block's rows are rows of block-row bi (columns of block-column bj when transposed)
     const int base = (transpose ? bj : bi) * MX_BS;
     const int row = t >> 2, kq = t & 3;           // kq: two groups of 8 K values each
     const int e_r = expo[base + row];
-    double sa[MX_S], sr[MX_S];
+    float sa[MX_S], sr[MX_S];                     // per-row sums of d_p^2 and (|R_p| + 1/2)^2
 #pragma unroll
-    for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.0;
+    for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.f;
     int firstp = MX_S + 1;
     uint8_t* out = slices + s * (int64_t)TILE_BYTES;
 #pragma unroll
     for (int g2 = 0; g2 < 2; ++g2) {
         const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
-        double rem[8];
+        int dig[8][MX_S];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) rem[e] = ldexp(T[row][kg * 8 + e], -e_r);
+        for (int e = 0; e < 8; ++e) {
+            // exact fixed point V = round(x 2^(63 - e_r)) from the bits of x
+            const long long bits = __double_as_longlong(T[row][kg * 8 + e]);
+            const int ex = (int)((bits >> 52) & 0x7FF);
+            long long m = bits & 0xFFFFFFFFFFFFFll;
+            int E;
+            if (ex == 0) {
+                E = -1074;
+            } else {
+                m |= 1ll << 52;
+                E = ex - 1075;
+            }
+            const int sh = E + 7 * MX_S - e_r;     // V = m 2^sh
+            long long V;
+            if (m == 0) V = 0;
+            else if (sh >= 0) V = m << sh;         // |x| < 2^e_r keeps this below 2^63
+            else if (sh > -63) V = (m + (1ll << (-sh - 1))) >> (-sh);
+            else V = 0;
+            if (bits < 0) V = -V;
+            long long rem = V;                     // digits from the bottom
+#pragma unroll
+            for (int p = MX_S - 1; p >= 1; --p) {
+                const long long d = ((rem + 64) & 127) - 64;
+                dig[e][p] = (int)d;
+                rem = (rem - d) >> 7;
+                // tail after digit p (in units of 2^(e_r - 63)): V - rem 2^(7(S - p))
+                const long long Rp = V - rem * (1ll << (MX_W * (MX_S - p)));
+                const float rf = fabsf((float)Rp) + 0.5f;
+                sr[p - 1] = fmaf(rf, rf, sr[p - 1]);
+            }
+            dig[e][0] = (int)rem;
+            sr[MX_S - 1] += 0.25f;                 // tail after all digits: |T_S| <= 1/2 unit
+        }
 #pragma unroll
         for (int p = 0; p < MX_S; ++p) {
             uint32_t packed[4];
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {
-                double t0 = rem[e] * 128.0, t1 = rem[e + 1] * 128.0;
-                double a0 = rint(t0), a1 = rint(t1);
-                rem[e] = t0 - a0;
-                rem[e + 1] = t1 - a1;
-                sa[p] = fma(a0, a0, fma(a1, a1, sa[p]));
-                if ((a0 != 0.0 || a1 != 0.0) && p + 1 < firstp) firstp = p + 1;
-                __nv_bfloat16 b0 = __float2bfloat16_rn((float)a0), b1 = __float2bfloat16_rn((float)a1);
+                const int a0 = dig[e][p], a1 = dig[e + 1][p];
+                sa[p] += (float)(a0 * a0 + a1 * a1);
+                if ((a0 | a1) != 0 && p + 1 < firstp) firstp = p + 1;
+                const __nv_bfloat16 b0 = __float2bfloat16_rn((float)a0);
+                const __nv_bfloat16 b1 = __float2bfloat16_rn((float)a1);
                 packed[e / 2] = (uint32_t)__bfloat16_as_ushort(b0) |
                                 ((uint32_t)__bfloat16_as_ushort(b1) << 16);
             }
-#pragma unroll
-            for (int e = 0; e < 8; ++e) sr[p] = fma(rem[e], rem[e], sr[p]);
-            // canonical offset: slice p, chunk kg/2, group row/8, k-core kg%2, row%8
             const int off = p * SLICE_BYTES + (kg >> 1) * CHUNK + (row >> 3) * 256 + (kg & 1) * 128 +
                             (row & 7) * 16;
             *reinterpret_cast<uint4*>(out + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
         }
     }
-    // scale by 2^(2(e_r - 7p)) and reduce over the block (fixed order)
+    // per-row sums -> scale by 2^(2(e_r - 7p)) (slice) or 2^(2(e_r - 63)) (tail) -> block sums
 #pragma unroll
     for (int p = 0; p < MX_S; ++p) {
-        const double sc = ldexp(1.0, 2 * (e_r - MX_W * (p + 1)));
-        double a = sa[p] * sc, r = sr[p] * sc;
+        double a = (double)sa[p] * ldexp(1.0, 2 * (e_r - MX_W * (p + 1)));
+        double r = (double)sr[p] * (1.0 + ldexp(1.0, -12)) * ldexp(1.0, 2 * (e_r - MX_W * MX_S));
         for (int o = 16; o > 0; o >>= 1) {
             a += __shfl_xor_sync(0xffffffffu, a, o);
             r += __shfl_xor_sync(0xffffffffu, r, o);
@@ -174,7 +208,7 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             r += red_r[w][t];
         }
         sn[s * MX_S + t] = sqrt(a);
-        tn[s * MX_S + t] = sqrt(r);
+        tn[s * MX_S + t] = sqrt(r) * (1.0 + ldexp(1.0, -40));
     }
     if (t == 0) p0[s] = (int8_t)first;
 }
@@ -240,17 +274,39 @@ __device__ __forceinline__ bool mx_keep(const ChargeData& ch, int i, int k, int 
     return charge(ch, *sa, *sb, ch.nB[(int64_t)k * nb + j]) < p;
 }
 
-__global__ void k_pair_count(ChargeData ch, const int32_t* __restrict__ out_flag,
+// Work items are enumerated in L2-friendly order: supertiles of IT row-block pairs
+// x JT block columns (IT * JT ~ one wave of CTAs), the column index fastest inside a
+// supertile. CTAs of one wave then share IT rows of A and JT columns of B while they
+// all walk k upwards, so operand slices are fetched from HBM about once per wave
+// instead of once per CTA.
+struct Raster {
+    int np, nb, it, jt, nsj;
+    __host__ __device__ int64_t size() const {
+        return (int64_t)((np + it - 1) / it) * it * (int64_t)nsj * jt;
+    }
+    __device__ bool unswizzle(int64_t b, int* I, int* j) const {
+        const int64_t per = (int64_t)it * jt;
+        const int64_t st = b / per;
+        const int r = (int)(b % per);
+        const int sI = (int)(st / nsj), sj = (int)(st % nsj);
+        *I = sI * it + r / jt;
+        *j = sj * jt + r % jt;
+        return *I < np && *j < nb;
+    }
+};
+
+__global__ void k_pair_count(ChargeData ch, Raster rs, const int32_t* __restrict__ out_flag,
                              const int32_t* __restrict__ mapX, int sym,
                              const double* __restrict__ d_tau, int32_t* __restrict__ cnt,
                              int32_t* __restrict__ wflag) {
-    const int nb = ch.nb, np = (nb + 1) / 2;
+    const int nb = ch.nb;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= (int64_t)np * nb) return;
-    const int I = (int)(b / nb), j = (int)(b % nb);
+    if (b >= rs.size()) return;
+    int I, j;
+    const bool valid = rs.unswizzle(b, &I, &j);
     const int i0 = 2 * I, i1 = 2 * I + 1;
     int c = 0, work = 0;
-    if (!sym || i0 <= j) {
+    if (valid && (!sym || i0 <= j)) {
         const double tau = *d_tau;
         for (int k = 0; k < nb; ++k) {
             int32_t sa, sb;
@@ -272,7 +328,7 @@ __device__ __forceinline__ int n_level_pairs(int pa, int qb, int L) {
     return n;
 }
 
-__global__ void k_pair_fill(ChargeData ch, const int32_t* __restrict__ out_flag,
+__global__ void k_pair_fill(ChargeData ch, Raster rs, const int32_t* __restrict__ out_flag,
                             const int64_t* __restrict__ out_idx, int sym,
                             const double* __restrict__ d_tau, const int32_t* __restrict__ wflag,
                             const int64_t* __restrict__ widx, const int64_t* __restrict__ toff,
@@ -280,14 +336,14 @@ __global__ void k_pair_fill(ChargeData ch, const int32_t* __restrict__ out_flag,
                             int64_t* __restrict__ work_off, int32_t* __restrict__ task,
                             const int8_t* __restrict__ p0A, const int8_t* __restrict__ p0B,
                             unsigned long long* __restrict__ counters) {
-    const int nb = ch.nb, np = (nb + 1) / 2;
+    const int nb = ch.nb;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long formed = 0, pairs = 0;
-    if (b < (int64_t)np * nb && wflag[b]) {
-        const int I = (int)(b / nb), j = (int)(b % nb);
+    int I = 0, j = 0;
+    if (b < rs.size() && wflag[b] && rs.unswizzle(b, &I, &j)) {
         const int i0 = 2 * I, i1 = 2 * I + 1;
         const int64_t w = widx[b];
-        work_ij[w] = (int32_t)b;
+        work_ij[w] = (int32_t)((int64_t)I * nb + j);
         const int64_t b0 = (int64_t)i0 * nb + j, b1 = (int64_t)i1 * nb + j;
         int32_t* wo = work_out + 4 * w;   // top, bottom, top mirror, bottom mirror
         wo[0] = out_flag[b0] ? (int32_t)out_idx[b0] : -1;
@@ -330,11 +386,12 @@ __global__ void k_last_off(int64_t* work_off, int64_t n_work, const int64_t* tof
 // ------------------------------------------------------ the tcgen05 kernel
 
 constexpr int GM_STAGES = 4;
-constexpr int STAGE_A = MX_S * 2 * CHUNK;   // 8 slices x (two 64-row chunks)
+constexpr int STAGE_A = MX_S * 2 * CHUNK;   // S slices x (two 64-row chunks)
 constexpr int STAGE_B = MX_S * CHUNK;
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
 constexpr int GM_THREADS = 18 * 32;         // warp 0 copies, warp 1 issues MMAs, 16 fold/epilogue
 constexpr int GM_SMEM = GM_STAGES * STAGE_BYTES + 1024;
+constexpr int MAX_LEVELS = 8;               // 8 x 64 = all 512 TMEM columns
 constexpr long long WAIT_LIMIT = 1ll << 22;
 
 struct MixedArgs {
@@ -350,9 +407,11 @@ struct MixedArgs {
     const int32_t* work_out;     // [4 * n_work]
     const int64_t* work_off;
     int nb;
-    int lmax;
+    int lv_lo, lv_hi;            // levels p + q formed by this pass (lv_hi - lv_lo < 8)
     int window;                  // leaf products per exact-accumulation window
     int mode;                    // 0: C; 1: Xn = C; 2: Xn = 2X - C
+    int raw_out;                 // 1: write this pass's raw product into the output slots
+    int add_prev;                // 1: add the raw product already in the output slots
     const int32_t* mapX;
     const double* tilesX;
     double* tilesC;
@@ -372,13 +431,14 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
     // bars: full[4], empty[4], acc_full, acc_empty, drain
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
     volatile int* s_err = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* hdr = reinterpret_cast<int*>(smem + GM_STAGES * STAGE_BYTES + 96);        // [4] pa | qb<<8
     double* red = reinterpret_cast<double*>(smem + GM_STAGES * STAGE_BYTES + 128);   // [16][3]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w = blockIdx.x;
     const int64_t t0 = a.work_off[w], t1 = a.work_off[w + 1];
     const int ntask = (int)(t1 - t0);
     const int nwin = (ntask + a.window - 1) / a.window;
-    const int L = a.lmax;
+    const int lo = a.lv_lo, hi = a.lv_hi;
     const uint32_t b_full = tc::smem_u32(bars), b_empty = tc::smem_u32(bars + 4);
     const uint32_t b_accf = tc::smem_u32(bars + 8), b_acce = tc::smem_u32(bars + 9);
     const uint32_t b_drain = tc::smem_u32(bars + 10);
@@ -400,39 +460,61 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------ producer (one lane)
-        if (lane == 0) {
-            int it = 0;
-            for (int64_t t = t0; t < t1 && !*s_err; ++t) {
-                const int32_t s0 = a.task[3 * t], s1 = a.task[3 * t + 1], sb = a.task[3 * t + 2];
-                const int pa = min(tile_p0(a.p0A, s0), tile_p0(a.p0A, s1));
-                const int qb = tile_p0(a.p0B, sb);
-                const int pmax = min(MX_S, L - qb), qmax = min(MX_S, L - pa);
+        // -------------------------------------------- producer (whole warp)
+        // lanes load the metadata of 32 tasks at a time; each stage's copies are
+        // issued by one lane each; lane 0 handles the barriers and the stage header
+        int it = 0;
+        bool ok = true;
+        for (int64_t base = t0; base < t1 && ok; base += 32) {
+            const int64_t tl = base + lane;
+            int32_t s0 = -1, s1 = -1, sb = 0;
+            int pa = MX_S + 1, qb = MX_S + 1;
+            if (tl < t1) {
+                s0 = a.task[3 * tl];
+                s1 = a.task[3 * tl + 1];
+                sb = a.task[3 * tl + 2];
+                pa = min(tile_p0(a.p0A, s0), tile_p0(a.p0A, s1));
+                qb = tile_p0(a.p0B, sb);
+            }
+            const int cnt = (int)min((int64_t)32, t1 - base);
+            for (int j = 0; j < cnt && ok; ++j) {
+                const int32_t js0 = __shfl_sync(0xffffffffu, s0, j);
+                const int32_t js1 = __shfl_sync(0xffffffffu, s1, j);
+                const int32_t jsb = __shfl_sync(0xffffffffu, sb, j);
+                const int jpa = __shfl_sync(0xffffffffu, pa, j);
+                const int jqb = __shfl_sync(0xffffffffu, qb, j);
+                const int pmax = min(MX_S, hi - jqb), qmax = min(MX_S, hi - jpa);
+                const int np = pmax >= jpa ? pmax - jpa + 1 : 0;
+                const int nq = qmax >= jqb ? qmax - jqb + 1 : 0;
                 for (int c = 0; c < 4; ++c, ++it) {
                     const int st = it % GM_STAGES;
-                    if (!tc::mbar_wait(b_empty + 8 * st, ((it / GM_STAGES) & 1) ^ 1, WAIT_LIMIT)) {
-                        atomicExch((int*)s_err, 1);
-                        break;
+                    bool got = true;
+                    if (lane == 0) {
+                        got = tc::mbar_wait(b_empty + 8 * st, ((it / GM_STAGES) & 1) ^ 1, WAIT_LIMIT);
+                        if (got) {
+                            hdr[st] = jpa | (jqb << 8);
+                            tc::mbar_arrive_expect_tx(b_full + 8 * st, (uint32_t)(2 * np + nq) * CHUNK);
+                        } else {
+                            atomicExch((int*)s_err, 1);
+                        }
                     }
-                    const int np = pmax >= pa ? pmax - pa + 1 : 0;
-                    const int nq = qmax >= qb ? qmax - qb + 1 : 0;
-                    tc::mbar_arrive_expect_tx(b_full + 8 * st, (uint32_t)(2 * np + nq) * CHUNK);
+                    ok = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+                    if (!ok) break;
                     const uint32_t sA = tc::smem_u32(stages + st * STAGE_BYTES);
                     const uint32_t sB = sA + STAGE_A;
-                    for (int p = pa; p <= pmax; ++p) {
-                        const uint8_t* g0 = s0 >= 0 ? a.slA + (int64_t)s0 * TILE_BYTES +
-                                                          (p - 1) * SLICE_BYTES + c * CHUNK
-                                                    : a.zero_chunk;
-                        const uint8_t* g1 = s1 >= 0 ? a.slA + (int64_t)s1 * TILE_BYTES +
-                                                          (p - 1) * SLICE_BYTES + c * CHUNK
-                                                    : a.zero_chunk;
-                        tc::bulk_g2s(sA + (p - 1) * 2 * CHUNK, g0, CHUNK, b_full + 8 * st);
-                        tc::bulk_g2s(sA + (p - 1) * 2 * CHUNK + CHUNK, g1, CHUNK, b_full + 8 * st);
-                    }
-                    for (int q = qb; q <= qmax; ++q)
+                    if (lane < 2 * np) {
+                        const int p = jpa + (lane >> 1), half = lane & 1;
+                        const int32_t sl = half ? js1 : js0;
+                        const uint8_t* g = sl >= 0 ? a.slA + (int64_t)sl * TILE_BYTES +
+                                                         (p - 1) * SLICE_BYTES + c * CHUNK
+                                                   : a.zero_chunk;
+                        tc::bulk_g2s(sA + (p - 1) * 2 * CHUNK + half * CHUNK, g, CHUNK, b_full + 8 * st);
+                    } else if (lane < 2 * np + nq) {
+                        const int q = jqb + (lane - 2 * np);
                         tc::bulk_g2s(sB + (q - 1) * CHUNK,
-                                     a.slB + (int64_t)sb * TILE_BYTES + (q - 1) * SLICE_BYTES + c * CHUNK,
+                                     a.slB + (int64_t)jsb * TILE_BYTES + (q - 1) * SLICE_BYTES + c * CHUNK,
                                      CHUNK, b_full + 8 * st);
+                    }
                 }
             }
         }
@@ -440,6 +522,8 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
         // ------------------------------------------------ MMA issuer (one lane)
         if (lane == 0) {
             constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+            const uint64_t dA0 = tc::desc_kmajor(tc::smem_u32(stages), 128, 256);
+            const uint64_t dB0 = tc::desc_kmajor(tc::smem_u32(stages + STAGE_A), 128, 256);
             int it = 0;
             int64_t t = t0;
             for (int win = 0; win < nwin && !*s_err; ++win) {
@@ -450,9 +534,6 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                 tc::fence_after();
                 const int64_t tend = min(t1, t + a.window);
                 for (; t < tend && !*s_err; ++t) {
-                    const int32_t s0 = a.task[3 * t], s1 = a.task[3 * t + 1], sb = a.task[3 * t + 2];
-                    const int pa = min(tile_p0(a.p0A, s0), tile_p0(a.p0A, s1));
-                    const int qb = tile_p0(a.p0B, sb);
                     for (int c = 0; c < 4; ++c, ++it) {
                         const int st = it % GM_STAGES;
                         if (!tc::mbar_wait(b_full + 8 * st, (it / GM_STAGES) & 1, WAIT_LIMIT)) {
@@ -460,14 +541,21 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                             break;
                         }
                         tc::fence_after();
-                        const uint32_t sA = tc::smem_u32(stages + st * STAGE_BYTES);
-                        const uint32_t sB = sA + STAGE_A;
-                        for (int p = pa; p <= MX_S && p + qb <= L; ++p)
-                            for (int q = qb; q <= MX_S && p + q <= L; ++q) {
-                                const uint64_t da = tc::desc_kmajor(sA + (p - 1) * 2 * CHUNK, 128, 256);
-                                const uint64_t db = tc::desc_kmajor(sB + (q - 1) * CHUNK, 128, 256);
-                                tc::mma_bf16(tmem + (uint32_t)(p + q - 2) * 64, da, db, idesc, 1u);
+                        const int h = hdr[st];
+                        const int pa = h & 0xff, qb = h >> 8;
+                        const uint64_t dAs = dA0 + (uint64_t)((st * STAGE_BYTES) >> 4);
+                        const uint64_t dBs = dB0 + (uint64_t)((st * STAGE_BYTES) >> 4);
+                        for (int p = pa; p <= MX_S && p + qb <= hi; ++p) {
+                            const uint64_t da = dAs + (uint64_t)(((p - 1) * 2 * CHUNK) >> 4);
+                            const int q0 = max(qb, lo - p), q1 = min(MX_S, hi - p);
+                            uint64_t db = dBs + (uint64_t)(((q0 - 1) * CHUNK) >> 4);
+                            uint32_t dcol = tmem + (uint32_t)(p + q0 - lo) * 64;
+                            for (int q = q0; q <= q1; ++q) {
+                                tc::mma_bf16(dcol, da, db, idesc, 1u);
+                                db += (uint64_t)(CHUNK >> 4);
+                                dcol += 64;
                             }
+                        }
                         tc::commit(b_empty + 8 * st);
                     }
                 }
@@ -485,24 +573,24 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
         long long H[16], Lo[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) H[j] = Lo[j] = 0;
-        for (int lv = 2; lv <= L; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - 2) * 64);
+        for (int lv = lo; lv <= hi; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - lo) * 64);
         tc::tmem_st_wait();
         tc::fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(b_acce);
         for (int win = 0; win < nwin; ++win) {
             if (__any_sync(0xffffffffu, *s_err != 0)) break;
-            const bool ok = tc::mbar_wait(b_accf, win & 1, WAIT_LIMIT);
+            const bool ok = tc::mbar_wait_sleep(b_accf, win & 1, WAIT_LIMIT);
             if (!__all_sync(0xffffffffu, ok)) {     // warp-uniform: tcgen05.ld/st are .aligned
                 if (lane == 0) atomicExch((int*)s_err, 5);
                 break;
             }
             tc::fence_after();
-            for (int lv = 2; lv <= L; ++lv) {
+            for (int lv = lo; lv <= hi; ++lv) {
                 uint32_t v[16];
-                tc::tmem_ld16(trow + (uint32_t)(lv - 2) * 64, v);
+                tc::tmem_ld16(trow + (uint32_t)(lv - lo) * 64, v);
                 tc::tmem_ld_wait();
-                const int sh = MX_W * (L - lv);     // weight of this level in V
+                const int sh = MX_W * (hi - lv);     // weight of this level in V
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const long long g = (long long)__float2int_rn(__uint_as_float(v[j]));
@@ -510,7 +598,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                     else H[j] += g << (sh - 28);
                 }
             }
-            for (int lv = 2; lv <= L; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - 2) * 64);
+            for (int lv = lo; lv <= hi; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - lo) * 64);
             tc::tmem_st_wait();
             tc::fence_before();
             __syncwarp();
@@ -540,7 +628,12 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                 const int sc = cb * 16 + j;
                 const int fs = a.expB[jb * MX_BS + sc];
                 const double v = fma((double)H[j], 268435456.0, (double)Lo[j]);   // H 2^28 + Lo
-                const double cv = ldexp(v, er + fs - MX_W * L);
+                double cv = ldexp(v, er + fs - MX_W * hi);
+                if (a.raw_out) {
+                    if (Co) Co[rr * MX_BS + sc] = cv;
+                    continue;
+                }
+                if (a.add_prev && Co) cv += Co[rr * MX_BS + sc];
                 const double x = X ? X[rr * MX_BS + sc] : 0.0;
                 const double out = a.mode == 2 ? 2.0 * x - cv : cv;
                 if (a.mode != 0) idem2 = fma(cv - x, cv - x, idem2);
@@ -563,7 +656,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
     }
     tc::fence_before();
     __syncthreads();
-    if (tid < 2) {
+    if (tid < 2 && !a.raw_out) {
         // half h: epilogue warps whose quarter is 2h or 2h+1, in warp order
         const int h = tid;
         double f = 0.0, tr = 0.0, id = 0.0;
@@ -585,8 +678,8 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
         const double nrm = sqrt(f);
         if (a.work_out[4 * w + h] >= 0) a.normC[(int64_t)bi * nb + jb] = nrm;
         if (ost >= 0) a.normC[(int64_t)jb * nb + bi] = nrm;
-        if (*s_err && h == 0) atomicExch(a.status, *s_err);
     }
+    if (tid == 0 && *s_err) atomicExch(a.status, *s_err);
     tc::fence_after();
     if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
@@ -695,7 +788,13 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     SP_TRY(plan_write_out_map(ctx, of, oidx, nb, C));
     // pair work items
     const int np = (nb + 1) / 2;
-    const int64_t npb = (int64_t)np * nb;
+    Raster rs;
+    rs.np = np;
+    rs.nb = nb;
+    rs.it = 8;
+    rs.jt = (ctx->num_sms + 7) / 8;
+    rs.nsj = (nb + rs.jt - 1) / rs.jt;
+    const int64_t npb = rs.size();
     int32_t *pc = nullptr, *pwf = nullptr;
     int64_t *ptoff = nullptr, *pwidx = nullptr;
     unsigned long long* d_tot = nullptr;
@@ -706,7 +805,7 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     SP_TRY(dalloc((void**)&d_tot, 16, s));
     const unsigned G = (unsigned)((npb + 255) / 256);
     ++ctx->launches;
-    k_pair_count<<<G, 256, 0, s>>>(ch, of, mode ? A->d_map : nullptr, sym, d_tau, pc, pwf);
+    k_pair_count<<<G, 256, 0, s>>>(ch, rs, of, mode ? A->d_map : nullptr, sym, d_tau, pc, pwf);
     SP_CHECK_LAUNCH();
     SP_TRY(scan_i32_to_i64(ctx, pc, ptoff, npb, d_tot));
     SP_TRY(scan_i32_to_i64(ctx, pwf, pwidx, npb, d_tot + 1));
@@ -726,7 +825,7 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     SP_TRY(dalloc((void**)&parts, sizeof(double) * 6 * nw, s));
     SP_CUDA(cudaMemsetAsync(&sc->mx_formed, 0, 2 * sizeof(unsigned long long), s));
     ++ctx->launches;
-    k_pair_fill<<<G, 256, 0, s>>>(ch, of, oidx, sym, d_tau, pwf, pwidx, ptoff, work_ij, work_out,
+    k_pair_fill<<<G, 256, 0, s>>>(ch, rs, of, oidx, sym, d_tau, pwf, pwidx, ptoff, work_ij, work_out,
                                   work_off, task, sa->p0, sbs->p0, &sc->mx_formed);
     ++ctx->launches;
     k_last_off<<<1, 1, 0, s>>>(work_off, n_work, ptoff, npb);
@@ -747,10 +846,6 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
         ga.work_out = work_out;
         ga.work_off = work_off;
         ga.nb = nb;
-        ga.lmax = lmax;
-        // exact window: per product, a level sum is below 2^18 (L + 1) (2^20 for L = 2)
-        const double per = ldexp(1.0, 18) * (lmax + 1 > 4 ? lmax + 1 : 4);
-        ga.window = (int)floor((ldexp(1.0, 24) - 1.0) / per);
         ga.mode = mode;
         ga.mapX = mode ? A->d_map : nullptr;
         ga.tilesX = mode ? A->d_tiles : nullptr;
@@ -768,6 +863,29 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
         }
         SP_CUDA(cudaMemsetAsync(&sc->status, 0, sizeof(int32_t), s));
         cudaEventRecord(ctx->ev[EV_PLAN1], s);
+        // levels above 9 do not fit in TMEM next to levels 2..9: a first pass forms them
+        // and leaves their (tiny) raw product in the output slots, the main pass adds it
+        auto window_for = [](int top) {
+            const double per = ldexp(1.0, 18) * (top + 1 > 4 ? top + 1 : 4);
+            return (int)floor((ldexp(1.0, 24) - 1.0) / per);
+        };
+        const int main_hi = lmax < 2 + MAX_LEVELS - 1 ? lmax : 2 + MAX_LEVELS - 1;
+        if (lmax > main_hi) {
+            MixedArgs gb = ga;
+            gb.lv_lo = main_hi + 1;
+            gb.lv_hi = lmax;
+            gb.window = window_for(lmax);
+            gb.raw_out = 1;
+            gb.add_prev = 0;
+            ++ctx->launches;
+            k_gemm_mixed<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(gb);
+            SP_CHECK_LAUNCH();
+        }
+        ga.lv_lo = 2;
+        ga.lv_hi = main_hi;
+        ga.window = window_for(main_hi);
+        ga.raw_out = 0;
+        ga.add_prev = lmax > main_hi ? 1 : 0;
         ++ctx->launches;
         k_gemm_mixed<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(ga);
         SP_CHECK_LAUNCH();

@@ -44,6 +44,25 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     return false;
 }
 
+// Bounded wait that sleeps between polls (for warps with nothing else to do, so that
+// they do not take issue slots from the warps that copy and issue MMAs).
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t bar, uint32_t parity, long long limit) {
+    unsigned ns = 32;
+    for (long long i = 0; i < limit; ++i) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, "
+            "0, p; }"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+    }
+    return false;
+}
+
 // 1-D bulk copy global -> shared, completion counted on an mbarrier (bytes % 16 == 0,
 // both addresses 16-byte aligned).
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,

@@ -34,7 +34,7 @@ def test_integer_products_are_exact(gctx, n, seed):
     A = g.integers(-100, 101, size=(n, n)).astype(np.float64)
     B = g.integers(-100, 101, size=(n, n)).astype(np.float64)
     C, rep = gctx.multiply_tau(gctx.from_dense(A, 64), gctx.from_dense(B, 64), 0.0, prec="mixed")
-    assert rep["lmax"] == 9
+    assert rep["lmax"] == 10
     np.testing.assert_array_equal(C.to_numpy(), A @ B)
 
 
