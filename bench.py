@@ -49,15 +49,23 @@ def parse():
     ap.add_argument("--variant", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-n", type=int, default=2048)
+    ap.add_argument("--input-cache", default=None,
+                    help="npz file holding the generated input (written when absent)")
     return ap.parse_args()
 
 
 # --------------------------------------------------------------- inputs
 
-def make_problem(n, use_gpu_eigh):
+def make_problem(n, use_gpu_eigh, cache=None):
     import numpy as np
 
     import synth
+    if cache and os.path.exists(cache):
+        z = np.load(cache)
+        P = synth.FockProblem(z["F"], int(z["n_occ"]), float(z["homo"]), float(z["lumo"]), 0.8, "eig")
+        P.occupied = z["occupied"]
+        P.eigvals = z["eigvals"]
+        return P
     eigh = None
     if use_gpu_eigh:
         import torch
@@ -71,6 +79,9 @@ def make_problem(n, use_gpu_eigh):
             return out
     P = synth.lattice_fock(n, seed=synth.SEED_BASE + 1, decay=0.8, gap=0.1, gap_mode="eig",
                            eigh=eigh, keep_vectors=True)
+    if cache:
+        np.savez(cache, F=P.F, n_occ=P.n_occ, homo=P.homo, lumo=P.lumo, occupied=P.occupied,
+                 eigvals=P.eigvals)
     return P
 
 
@@ -178,7 +189,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return 0
     import numpy as np
-    P = make_problem(args.n, use_gpu_eigh=False)
+    P = make_problem(args.n, use_gpu_eigh=False, cache=args.input_cache)
     lmin, lmax = gershgorin_np(P.F)
     X0 = x0_of(P.F, lmin, lmax)
     width = lmax - lmin
@@ -225,7 +236,7 @@ def run_ours(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    P = make_problem(args.n, use_gpu_eigh=True)
+    P = make_problem(args.n, use_gpu_eigh=True, cache=args.input_cache)
     n, bs = args.n, args.bs
     F_host = torch.from_numpy(P.F).pin_memory()
     D_host = torch.empty((n, n), dtype=torch.float64).pin_memory()
@@ -330,6 +341,7 @@ def run_ours(args, rank, world):
                        "parallelism": f"replicas x{world}"},
             "spamm_ms": spamm_ms,
             "iters": rep0["iters"], "converged": rep0["converged"],
+            "step_slice_levels": rep0["step_lmax"],
             "check": {"d_minus_exact_fro": d_err, "eps": args.eps},
             "phase_ms": {"cse": sum(r["ms_phase"][1] for r in reps) / args.steps,
                          "plan": sum(r["ms_phase"][2] for r in reps) / args.steps,

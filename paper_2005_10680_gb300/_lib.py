@@ -336,5 +336,5 @@ class Context:
              "deltas": logs["delta"][:it].tolist(), "taus": logs["tau"][:it].tolist(),
              "traces": logs["trace"][:it].tolist(), "idems": logs["idem"][:it].tolist(),
              "branches": br[:it].tolist(), "nnzb": nz[:it].tolist(),
-             "lmax": lm[:it].tolist(), "step_ms": sms[:it].tolist()}
+             "step_lmax": lm[:it].tolist(), "step_ms": sms[:it].tolist()}
         return Matrix(self, out.value), r

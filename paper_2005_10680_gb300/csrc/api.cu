@@ -99,6 +99,13 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
                 err_charge = ec;
                 break;
             }
+            // at the most levels, let the charge take up to 0.9 delta (the tau search
+            // still certifies charge plus skipped products below delta)
+            if (L == 10 && ec <= 0.9 * delta) {
+                lmax_used = L;
+                err_charge = ec;
+                break;
+            }
         }
         if (st == SPAMM_OK && lmax_used == 0) {
             // the slices cannot certify delta: fall back to float64 leaf products
