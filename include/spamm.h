@@ -226,6 +226,19 @@ typedef struct {
 int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, double eps, int n_iter,
                  const spamm_purify_opts* opts, spamm_mat** D, spamm_purify_report* rep);
 
+/* Batched purification: `count` independent problems F[i] (each with its own
+   n, n_occ[i] and opts[i]; eps and n_iter shared) purified concurrently by
+   `workers` host threads, each with its own CUDA stream on ctx's device, so the
+   kernels of different problems overlap. Each problem follows spamm_purify
+   exactly (identical results). Outputs: D[i] (caller frees), reps[i] (optional;
+   its step-log pointers are used as given), status[i] = spamm_purify's status.
+   Returns SPAMM_OK when every problem returned SPAMM_OK or SPAMM_ENOTCONV,
+   else the status of a failing problem. */
+int spamm_purify_batched(spamm_ctx* ctx, int count, const spamm_mat* const* F,
+                         const int64_t* n_occ, double eps, int n_iter,
+                         const spamm_purify_opts* opts, int workers, spamm_mat** D,
+                         spamm_purify_report* reps, int32_t* status);
+
 #ifdef __cplusplus
 }
 #endif

@@ -103,6 +103,8 @@ def load_library(build_if_stale: bool = True):
         "spamm_truncate": ([vp, vp, d, i32, P(Report)], i32),
         "spamm_purify": ([vp, vp, i64, d, i32, P(PurifyOpts), P(vp), P(PurifyReport)], i32),
         "spamm_cse_search_noalloc": ([vp, vp, i64, d, vp, vp, vp, vp], i32),
+        "spamm_purify_batched": ([vp, i32, P(vp), P(i64), d, i32, P(PurifyOpts), i32, P(vp),
+                                  P(PurifyReport), P(ctypes.c_int32)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -338,3 +340,26 @@ class Context:
              "branches": br[:it].tolist(), "nnzb": nz[:it].tolist(),
              "step_lmax": lm[:it].tolist(), "step_ms": sms[:it].tolist()}
         return Matrix(self, out.value), r
+
+    def purify_batched(self, Fs, n_occ, eps: float, n_iter: int, homo, lumo, variant: int = HYBRID,
+                       prec="fp64", workers: int = 8):
+        """Purify independent problems concurrently (see spamm_purify_batched)."""
+        count = len(Fs)
+        FA = (ctypes.c_void_p * count)(*[F.handle.value for F in Fs])
+        NO = (ctypes.c_int64 * count)(*[int(x) for x in n_occ])
+        OP = (PurifyOpts * count)(*[PurifyOpts(variant, _PREC[prec], float(h), float(l), 0, 0.0, 0.0)
+                                    for h, l in zip(homo, lumo)])
+        DA = (ctypes.c_void_p * count)()
+        RE = (PurifyReport * count)()
+        ST = (ctypes.c_int32 * count)()
+        st = _lib.spamm_purify_batched(self.handle, count, FA, NO, float(eps), int(n_iter), OP,
+                                       int(workers), DA, RE, ST)
+        _check(st, "spamm_purify_batched", allow=(5,))
+        out = []
+        for i in range(count):
+            r = RE[i]
+            out.append((Matrix(self, DA[i]), {"iters": r.iters, "converged": bool(r.converged),
+                                              "status": int(ST[i]), "idem": r.idem,
+                                              "trace": r.trace, "ms_total": r.ms_total,
+                                              "kept_total": r.kept_total}))
+        return out

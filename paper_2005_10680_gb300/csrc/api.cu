@@ -81,30 +81,50 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         }
         cudaEventRecord(ctx->ev[EV_CSE0], s);
         // fewest levels whose certified charge (everything kept, tau = 0) stays within
-        // half of delta; with a given tau every level up to 10 is formed
+        // half of delta: the charge shrinks as levels are added, so bisect over
+        // L in [4, 10]; with a given tau every level up to 10 is formed. At L = 10 the
+        // charge may take up to 0.9 delta (the tau search still certifies the sum of
+        // charges and skipped products below delta).
         lmax_used = 0;
-        const int first = search ? 4 : 10;
-        for (int L = first; L <= 10 && st == SPAMM_OK; ++L) {
+        auto charge_at = [&](int L, double* ec) -> int {
             ChargeData ch = mixed_charge(A, B, nA, nB, mp, L);
             ++ctx->launches;
             k_set_tau<<<1, 1, 0, s>>>(sc, 0.0);
-            st = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_charge, ch);
-            if (st != SPAMM_OK) break;
-            double ec = 0.0;
-            cudaMemcpyAsync(&ec, &sc->err_charge, 8, cudaMemcpyDeviceToHost, s);
+            int r = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_charge, ch);
+            if (r != SPAMM_OK) return r;
+            cudaMemcpyAsync(ec, &sc->err_charge, 8, cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
             ++evals;
-            if (!search || ec <= 0.5 * delta) {
-                lmax_used = L;
-                err_charge = ec;
-                break;
+            return SPAMM_OK;
+        };
+        if (!search) {
+            double ec = 0.0;
+            st = charge_at(10, &ec);
+            lmax_used = 10;
+            err_charge = ec;
+        } else {
+            int lo = 4, hi = 10;
+            double ec_hi = -1.0;
+            while (lo < hi && st == SPAMM_OK) {
+                const int mid = (lo + hi) / 2;
+                double ec = 0.0;
+                st = charge_at(mid, &ec);
+                if (st != SPAMM_OK) break;
+                if (ec <= 0.5 * delta) {
+                    hi = mid;
+                    ec_hi = ec;
+                } else {
+                    lo = mid + 1;
+                }
             }
-            // at the most levels, let the charge take up to 0.9 delta (the tau search
-            // still certifies charge plus skipped products below delta)
-            if (L == 10 && ec <= 0.9 * delta) {
-                lmax_used = L;
-                err_charge = ec;
-                break;
+            if (st == SPAMM_OK) {
+                double ec = ec_hi;
+                if (ec < 0.0) st = charge_at(lo, &ec);   // lo == 10 was never evaluated
+                if (st == SPAMM_OK &&
+                    (ec <= 0.5 * delta || (lo == 10 && ec <= 0.9 * delta))) {
+                    lmax_used = lo;
+                    err_charge = ec;
+                }
             }
         }
         if (st == SPAMM_OK && lmax_used == 0) {

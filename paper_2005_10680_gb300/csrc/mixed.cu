@@ -31,6 +31,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -687,8 +688,11 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
 // ------------------------------------------------------------- host side
 
 static uint8_t* g_zero_chunk[64] = {nullptr};
+static bool g_attr_set[64] = {false};
+static std::mutex g_mixed_init;   // one-time per-device set-up, shared by host threads
 
 static int zero_chunk(spamm_ctx* ctx, const uint8_t** out) {
+    std::lock_guard<std::mutex> lock(g_mixed_init);
     if (!g_zero_chunk[ctx->device]) {
         uint8_t* p = nullptr;
         SP_CUDA(cudaMalloc(&p, CHUNK));
@@ -855,11 +859,13 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
         ga.part_trace = parts + 2 * nw;
         ga.part_idem2 = parts + 4 * nw;
         ga.status = &sc->status;
-        static bool attr_set[64] = {false};
-        if (!attr_set[ctx->device]) {
-            SP_CUDA(cudaFuncSetAttribute(k_gemm_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         GM_SMEM));
-            attr_set[ctx->device] = true;
+        {
+            std::lock_guard<std::mutex> lock(g_mixed_init);
+            if (!g_attr_set[ctx->device]) {
+                SP_CUDA(cudaFuncSetAttribute(k_gemm_mixed,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
+                g_attr_set[ctx->device] = true;
+            }
         }
         SP_CUDA(cudaMemsetAsync(&sc->status, 0, sizeof(int32_t), s));
         cudaEventRecord(ctx->ev[EV_PLAN1], s);
