@@ -182,6 +182,25 @@ def scalar_sp2_steps(F_eigs, n_occ, eps, n_iter, lmin, lmax):
     return n_iter
 
 
+# ------------------------------------------------------- rank aggregation
+
+def max_over_ranks(vals, dist=None, device="cpu"):
+    """Element-wise maximum over the ranks (every rank times its own replicas)."""
+    if dist is None or not dist.is_initialized():
+        return list(vals)
+    import torch
+    t = torch.tensor(list(vals), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def per_purification(sums_ms, world, steps):
+    """Whole-job ms per purification: the slowest rank's time over all purifications
+    of all ranks (replicas: each rank purifies its own copy, no data exchange)."""
+    units = world * steps
+    return [v / units for v in sums_ms]
+
+
 # ---------------------------------------------------------------- arms
 
 def run_reference(args, rank, world):
@@ -290,15 +309,8 @@ def run_ours(args, rank, world):
     total_ms = t_start.elapsed_time(t_end)
     dev_ms = [e[1].elapsed_time(e[2]) for e in evs]
     e2e_ms = [e[0].elapsed_time(e[3]) for e in evs]
-    if dist is not None:
-        t = torch.tensor([sum(dev_ms), sum(e2e_ms), total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sum_dev, sum_e2e, total_ms = t.tolist()
-    else:
-        sum_dev, sum_e2e = sum(dev_ms), sum(e2e_ms)
-    units = world * args.steps                      # purifications done by the whole job
-    value = sum_dev / units
-    e2e = sum_e2e / units
+    sum_dev, sum_e2e, total_ms = max_over_ranks([sum(dev_ms), sum(e2e_ms), total_ms], dist, "cuda")
+    value, e2e = per_purification([sum_dev, sum_e2e], world, args.steps)
 
     # correctness of the last step against the eigendecomposition (not timed)
     Dt = D_host.cuda()
