@@ -9,6 +9,17 @@ products with the fused SP2 epilogue, truncation) runs inside it, on the GPU.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--form fp64|mixed|auto]
     python bench.py --impl reference      # the CPU oracle arm
+    python bench.py --protocol            # the paper's two-squares experiment
+
+--protocol runs the experiment of the paper's Section 5 on a converged density
+matrix D (this path's own purification of the same Fock matrix): for each
+tolerance delta and each of truncmul (Algorithm 1's multiply-then-truncate),
+SpAMM (Algorithm 4) and hybrid (Algorithm 5), X1 = approximate square of D,
+X2 = approximate square of X1 at the same delta; the second square is timed
+(T_mul, T_trunc, T_SpAMM, T_CSE as in Fig. 1), the block fill of X1, of the
+product before truncation and of X2 is reported (Fig. 2), and ||X2 - X1^2||_F
+against the exact float64 square of X1 (Fig. 3). One JSON line per (variant,
+delta).
 
 Prints one JSON line (rank 0). Timing: CUDA events on the library's stream,
 barrier + synchronize on both sides of the K timed steps; inputs (2.1 GB per
@@ -49,6 +60,9 @@ def parse():
     ap.add_argument("--variant", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sample-n", type=int, default=2048)
+    ap.add_argument("--protocol", action="store_true",
+                    help="run the two-squares experiment instead of the purification bench")
+    ap.add_argument("--deltas", default="1e-2,1e-4,1e-6,1e-8")
     ap.add_argument("--input-cache", default=None,
                     help="npz file holding the generated input (written when absent)")
     return ap.parse_args()
@@ -387,8 +401,91 @@ def run_ours(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------- two-squares protocol
+
+PROTOCOL_VARIANTS = (("truncmul", 1), ("spamm", 4), ("hybrid", 5))
+
+
+def approx_square(ctx, X, delta, variant, prec):
+    """One approximate square X^2 with ||error||_F < delta by Algorithm 1's
+    multiply + truncation (variant 1), SpAMM (4) or SpAMM at delta/2 plus
+    truncation at delta/2 (5). Returns the product and the phase times (ms)
+    and block counts of this square."""
+    if variant == 1:
+        Y, rep = ctx.sp2_step(X, 0, 0.0, 0.0, prec=prec)
+    else:
+        Y, rep = ctx.sp2_step(X, 0, delta if variant == 4 else 0.5 * delta, prec=prec)
+    ms = rep["ms"]
+    out = {"t_mul_ms": ms[6] if variant == 1 else 0.0,
+           "t_spamm_ms": 0.0 if variant == 1 else ms[6] - ms[1],
+           "t_cse_ms": 0.0 if variant == 1 else ms[1],
+           "t_trunc_ms": 0.0, "nnzb_product": Y.nnzb, "tau": rep["tau"],
+           "bound": rep["bound"], "bound_round": rep["bound_round"]}
+    if variant in (1, 5):
+        tr = ctx.truncate(Y, delta if variant == 1 else 0.5 * delta)
+        out["t_trunc_ms"] = tr["ms"][4]
+    out["nnzb_out"] = Y.nnzb
+    return Y, out
+
+
+def fro_diff(A, B):
+    """||A - B||_F of two device matrices, read back densely (a check, not a step of
+    the path)."""
+    import torch
+    a, b = A.to_torch(), B.to_torch()
+    d = float(torch.linalg.norm(a - b))
+    del a, b
+    return d
+
+
+def square_twice(ctx, D, delta, variant, prec):
+    """The paper's protocol for one (variant, delta): square D, square the result
+    again at the same delta, time the second square and check it against the exact
+    float64 square of its input."""
+    X1, _ = approx_square(ctx, D, delta, variant, prec)
+    X2, out = approx_square(ctx, X1, delta, variant, prec)
+    exact, _ = ctx.sp2_step(X1, 0, 0.0, 0.0, prec="fp64")
+    err = fro_diff(X2, exact)
+    nb2 = D.nb * D.nb
+    out.update({"nnz_pct": {"X_in": 100.0 * X1.nnzb / nb2,
+                            "product": 100.0 * out.pop("nnzb_product") / nb2,
+                            "X_out": 100.0 * out.pop("nnzb_out") / nb2},
+                "err": err, "err_over_delta": err / delta})
+    return out
+
+
+def run_protocol(args):
+    import torch
+
+    import paper_2005_10680_gb300 as sp
+    torch.cuda.set_device(0)
+    P = make_problem(args.n, use_gpu_eigh=True, cache=args.input_cache)
+    stream = torch.cuda.Stream()
+    ctx = sp.Context(0, stream=stream)
+    fastest = "mixed" if ctx.supports("mixed", args.bs) else "fp64"
+    forms = [args.form] if args.form != "auto" else sorted({fastest, "fp64"})
+    F = ctx.from_dense(torch.from_numpy(P.F), bs=args.bs)
+    D, rep = ctx.purify(F, P.n_occ, args.eps, args.n_iter, P.homo, P.lumo,
+                        variant=args.variant, prec=fastest, strict=False)
+    del F
+    for form in forms:
+        for delta in [float(x) for x in args.deltas.split(",")]:
+            for name, v in PROTOCOL_VARIANTS:
+                out = square_twice(ctx, D, delta, v, form)
+                line = {"protocol": "two squares of a converged D", "variant": name,
+                        "algorithm": v, "delta": delta, "form": form, "n": args.n,
+                        "bs": args.bs,
+                        "D": f"SP2 purification (Algorithm {args.variant}, {fastest}) of the "
+                             f"bench's Fock matrix, eps {args.eps}, {rep['iters']} iterations"}
+                line.update(out)
+                print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.protocol:
+        return run_protocol(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

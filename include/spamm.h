@@ -226,6 +226,24 @@ typedef struct {
 int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, double eps, int n_iter,
                  const spamm_purify_opts* opts, spamm_mat** D, spamm_purify_report* rep);
 
+/* Autotuner (the leaf size and arithmetic of the leaf products are left open by
+   the paper, whose leaf level is a CPU library's 2048 x 2048 blocks). Times one
+   SP2 product X^2 with error control at delta for each candidate -- float64 leaf
+   products with bs = 32, 64, 128, and the mixed form (bs = 64) when allow_mixed --
+   on the leading principal block of X (at most 4096 x 4096) re-blocked on the
+   device, and returns the fastest. Answers are cached per device by (n, block
+   fill of X, floor(log10 delta), allow_mixed); out->cached says whether this call
+   was answered from the cache. ms[c] < 0: candidate not run. */
+typedef struct {
+    int32_t bs;
+    spamm_prec prec;
+    float ms[4];             /* float64 bs 32, 64, 128; mixed bs 64 */
+    int32_t cached;
+} spamm_tune_result;
+
+int spamm_autotune(spamm_ctx* ctx, const spamm_mat* X, double delta, int allow_mixed,
+                   spamm_tune_result* out);
+
 /* Batched purification: `count` independent problems F[i] (each with its own
    n, n_occ[i] and opts[i]; eps and n_iter shared) purified concurrently by
    `workers` host threads, each with its own CUDA stream on ctx's device, so the

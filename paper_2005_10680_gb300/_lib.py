@@ -38,6 +38,11 @@ class Report(ctypes.Structure):
         return d
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("bs", ctypes.c_int32), ("prec", ctypes.c_int), ("ms", ctypes.c_float * 4),
+                ("cached", ctypes.c_int32)]
+
+
 class PurifyOpts(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("prec", ctypes.c_int), ("homo", ctypes.c_double),
                 ("lumo", ctypes.c_double), ("have_bounds", ctypes.c_int),
@@ -103,6 +108,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_truncate": ([vp, vp, d, i32, P(Report)], i32),
         "spamm_purify": ([vp, vp, i64, d, i32, P(PurifyOpts), P(vp), P(PurifyReport)], i32),
         "spamm_cse_search_noalloc": ([vp, vp, i64, d, vp, vp, vp, vp], i32),
+        "spamm_autotune": ([vp, vp, d, i32, P(TuneResult)], i32),
         "spamm_purify_batched": ([vp, i32, P(vp), P(i64), d, i32, P(PurifyOpts), i32, P(vp),
                                   P(PurifyReport), P(ctypes.c_int32)], i32),
     }
@@ -363,3 +369,12 @@ class Context:
                                               "trace": r.trace, "ms_total": r.ms_total,
                                               "kept_total": r.kept_total}))
         return out
+
+    def autotune(self, X: Matrix, delta: float, allow_mixed: bool = True):
+        """Fastest leaf size / arithmetic for X (see spamm_autotune)."""
+        r = TuneResult()
+        _check(_lib.spamm_autotune(self.handle, X.handle, float(delta), int(bool(allow_mixed)),
+                                   ctypes.byref(r)), "spamm_autotune")
+        return {"bs": r.bs, "prec": "mixed" if r.prec == MIXED else "fp64",
+                "ms": {"fp64_bs32": r.ms[0], "fp64_bs64": r.ms[1], "fp64_bs128": r.ms[2],
+                       "mixed_bs64": r.ms[3]}, "cached": bool(r.cached)}

@@ -69,7 +69,7 @@ struct spamm_mat {
 namespace spamm {
 
 // indices into spamm_ctx::ev (phase timers of one multiply)
-enum { EV_T0 = 0, EV_CSE0, EV_CSE1, EV_PLAN1, EV_GEMM1, EV_END, EV_TR0, EV_TR1 };
+enum { EV_T0 = 0, EV_CSE0, EV_CSE1, EV_PLAN1, EV_GEMM1, EV_END, EV_TR0, EV_TR1, EV_TUNE0, EV_TUNE1 };
 
 // Device scalars of one multiply/purification step (single struct so one copy
 // brings everything back to the host).
