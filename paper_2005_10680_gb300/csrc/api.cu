@@ -82,7 +82,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         cudaEventRecord(ctx->ev[EV_CSE0], s);
         // fewest levels whose certified charge (everything kept, tau = 0) stays within
         // half of delta: the charge shrinks as levels are added, so bisect over
-        // L in [4, 10]; with a given tau every level up to 10 is formed. At L = 10 the
+        // L in [4, 11]; with a given tau every level up to 10 is formed. At L = 11 the
         // charge may take up to 0.9 delta (the tau search still certifies the sum of
         // charges and skipped products below delta).
         lmax_used = 0;
@@ -103,7 +103,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
             lmax_used = 10;
             err_charge = ec;
         } else {
-            int lo = 4, hi = 10;
+            int lo = 4, hi = MIXED_LMAX;
             double ec_hi = -1.0;
             while (lo < hi && st == SPAMM_OK) {
                 const int mid = (lo + hi) / 2;
@@ -119,9 +119,9 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
             }
             if (st == SPAMM_OK) {
                 double ec = ec_hi;
-                if (ec < 0.0) st = charge_at(lo, &ec);   // lo == 10 was never evaluated
+                if (ec < 0.0) st = charge_at(lo, &ec);   // lo == MIXED_LMAX was never evaluated
                 if (st == SPAMM_OK &&
-                    (ec <= 0.5 * delta || (lo == 10 && ec <= 0.9 * delta))) {
+                    (ec <= 0.5 * delta || (lo == MIXED_LMAX && ec <= 0.9 * delta))) {
                     lmax_used = lo;
                     err_charge = ec;
                 }

@@ -99,8 +99,8 @@ __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __re
 //     d = ((V + 64) mod 128) - 64 in [-64, 63], V <- (V - d) / 128, ..., d_1 = V,
 // so x = sum_p d_p 2^(e_r - 7p) + T_9 with |d_1| <= 128, |T_9| <= 2^(e_r - 64).
 // Slice norms are exact (digit squares summed exactly per row in f32); tail norms
-// are upper bounds: (|R_p| + 1/2) per entry, summed in f32 and inflated by 2^-12
-// to cover the f32 rounding. transpose: slice the transposed block with column
+// are upper bounds: |R_p| per entry, plus 1/2 where the rounding of V was inexact,
+// summed in f32 and inflated by 2^-12 to cover the f32 rounding. transpose: slice the transposed block with column
 // exponents.
 __global__ void __launch_bounds__(256)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
@@ -149,11 +149,18 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             }
             const int sh = E + 7 * MX_S - e_r;     // V = m 2^sh
             long long V;
+            bool inexact = false;                  // V != x 2^(63 - e_r)
             if (m == 0) V = 0;
             else if (sh >= 0) V = m << sh;         // |x| < 2^e_r keeps this below 2^63
-            else if (sh > -63) V = (m + (1ll << (-sh - 1))) >> (-sh);
-            else V = 0;
+            else if (sh > -63) {
+                V = (m + (1ll << (-sh - 1))) >> (-sh);
+                inexact = (m & ((1ll << (-sh)) - 1)) != 0;
+            } else {
+                V = 0;
+                inexact = true;
+            }
             if (bits < 0) V = -V;
+            const float half = inexact ? 0.5f : 0.f;
             long long rem = V;                     // digits from the bottom
 #pragma unroll
             for (int p = MX_S - 1; p >= 1; --p) {
@@ -162,11 +169,11 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                 rem = (rem - d) >> 7;
                 // tail after digit p (in units of 2^(e_r - 63)): V - rem 2^(7(S - p))
                 const long long Rp = V - rem * (1ll << (MX_W * (MX_S - p)));
-                const float rf = fabsf((float)Rp) + 0.5f;
+                const float rf = fabsf((float)Rp) + half;
                 sr[p - 1] = fmaf(rf, rf, sr[p - 1]);
             }
             dig[e][0] = (int)rem;
-            sr[MX_S - 1] += 0.25f;                 // tail after all digits: |T_S| <= 1/2 unit
+            sr[MX_S - 1] += half * half;           // tail after all digits: |T_S| <= 1/2 unit
         }
 #pragma unroll
         for (int p = 0; p < MX_S; ++p) {

@@ -115,3 +115,25 @@ def test_mixed_purify_matches_eigendecomposition(gctx, orc, variant, gap_mode, n
                            variant=variant, prec="fp64")
     assert abs(rep["iters"] - repf["iters"]) <= 1
     assert np.linalg.norm(got - Df.to_numpy()) < eps
+
+
+def test_eleventh_level_when_ten_cannot_certify(gctx, orc):
+    # delta just above the level-10 charge: level 10 no longer fits in half of delta,
+    # so the search forms level 11 (second pass) and still certifies delta
+    n = 1024
+    P = synth.lattice_fock(n, seed=41, gap_mode="stagger")
+    lmin, lmax = orc.gershgorin(P.F)
+    X = (lmax * np.eye(n) - P.F) / (lmax - lmin)
+    G = gctx.from_dense(X, 64)
+    C10, r10 = gctx.multiply_tau(G, G, 0.0, prec="mixed")
+    assert r10["lmax"] == 10 and r10["bound_round"] > 0
+    delta = 1.2 * r10["bound_round"]
+    C, rep = gctx.sp2_step(G, 0, delta=delta, prec="mixed")
+    assert rep["lmax"] == 11
+    assert rep["bound_round"] < 0.1 * r10["bound_round"]
+    assert rep["bound"] < delta
+    # both products are integers rounded once or twice to float64 at the end: each
+    # is within its bound of X X, up to two roundings of the output
+    c10 = C10.to_numpy()
+    out_round = 2.3e-16 * np.linalg.norm(c10)
+    assert np.linalg.norm(C.to_numpy() - c10) <= rep["bound"] + r10["bound"] + 2 * out_round
