@@ -40,7 +40,6 @@ namespace spamm {
 
 constexpr int MX_W = 7;
 constexpr int MX_S = MX_SLICES;
-constexpr int MX_LMAX = 10;
 constexpr int MX_BS = 64;
 constexpr int CHUNK = 2048;                      // 64 rows x 16 K x 2 bytes
 constexpr int SLICE_BYTES = 4 * CHUNK;           // one slice of one 64 x 64 block
@@ -432,7 +431,11 @@ struct MixedArgs {
 
 __device__ __forceinline__ int tile_p0(const int8_t* p0, int32_t s) { return s >= 0 ? p0[s] : MX_S + 1; }
 
+// LO..HI: the levels p + q this pass forms (compile time, so that the MMA issue loop
+// unrolls into constant descriptor offsets)
+template <int LO, int HI>
 __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
+    static_assert(HI - LO < MAX_LEVELS && LO >= 2 && HI <= 2 * MX_S, "levels must fit in TMEM");
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* stages = smem;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + GM_STAGES * STAGE_BYTES);
@@ -446,7 +449,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
     const int64_t t0 = a.work_off[w], t1 = a.work_off[w + 1];
     const int ntask = (int)(t1 - t0);
     const int nwin = (ntask + a.window - 1) / a.window;
-    const int lo = a.lv_lo, hi = a.lv_hi;
+    constexpr int lo = LO, hi = HI;
     const uint32_t b_full = tc::smem_u32(bars), b_empty = tc::smem_u32(bars + 4);
     const uint32_t b_accf = tc::smem_u32(bars + 8), b_acce = tc::smem_u32(bars + 9);
     const uint32_t b_drain = tc::smem_u32(bars + 10);
@@ -527,51 +530,77 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer (one lane)
-        if (lane == 0) {
-            constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
-            const uint64_t dA0 = tc::desc_kmajor(tc::smem_u32(stages), 128, 256);
-            const uint64_t dB0 = tc::desc_kmajor(tc::smem_u32(stages + STAGE_A), 128, 256);
-            int it = 0;
-            int64_t t = t0;
-            for (int win = 0; win < nwin && !*s_err; ++win) {
-                if (!tc::mbar_wait(b_acce, win & 1, WAIT_LIMIT)) {
-                    atomicExch((int*)s_err, 2);
-                    break;
-                }
-                tc::fence_after();
-                const int64_t tend = min(t1, t + a.window);
-                for (; t < tend && !*s_err; ++t) {
-                    for (int c = 0; c < 4; ++c, ++it) {
-                        const int st = it % GM_STAGES;
-                        if (!tc::mbar_wait(b_full + 8 * st, (it / GM_STAGES) & 1, WAIT_LIMIT)) {
-                            atomicExch((int*)s_err, 3);
-                            break;
-                        }
-                        tc::fence_after();
-                        const int h = hdr[st];
-                        const int pa = h & 0xff, qb = h >> 8;
-                        const uint64_t dAs = dA0 + (uint64_t)((st * STAGE_BYTES) >> 4);
-                        const uint64_t dBs = dB0 + (uint64_t)((st * STAGE_BYTES) >> 4);
-                        for (int p = pa; p <= MX_S && p + qb <= hi; ++p) {
+        // ------------------------------------- MMA issuer (converged warp)
+        // The whole warp runs the loop so that its control stays warp-uniform; one
+        // elected lane issues the MMAs and the commits.
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+        const uint64_t dA0 = tc::desc_kmajor(tc::smem_u32(stages), 128, 256);
+        const uint64_t dB0 = tc::desc_kmajor(tc::smem_u32(stages + STAGE_A), 128, 256);
+        const uint32_t e = tc::elect_one();
+        int it = 0;
+        int64_t t = t0;
+        bool ok = true;
+        for (int win = 0; win < nwin && ok; ++win) {
+            ok = __all_sync(0xffffffffu, tc::mbar_wait(b_acce, win & 1, WAIT_LIMIT));
+            if (!ok) {
+                if (e) atomicExch((int*)s_err, 2);
+                break;
+            }
+            tc::fence_after();
+            const int64_t tend = min(t1, t + a.window);
+            for (; t < tend && ok; ++t) {
+                for (int c = 0; c < 4; ++c, ++it) {
+                    const int st = it % GM_STAGES;
+                    ok = __all_sync(0xffffffffu,
+                                    tc::mbar_wait(b_full + 8 * st, (it / GM_STAGES) & 1, WAIT_LIMIT));
+                    if (!ok) {
+                        if (e) atomicExch((int*)s_err, 3);
+                        break;
+                    }
+                    tc::fence_after();
+                    const int h = hdr[st];
+                    const int pa = h & 0xff, qb = h >> 8;
+                    const uint64_t dAs = dA0 + (uint64_t)((st * STAGE_BYTES) >> 4);
+                    const uint64_t dBs = dB0 + (uint64_t)((st * STAGE_BYTES) >> 4);
+                    if constexpr (LO == 2) {
+                        // many (p, q) per level: loops whose trip counts follow pa, qb
+                        for (int p = pa; p <= MX_S && p + qb <= HI; ++p) {
                             const uint64_t da = dAs + (uint64_t)(((p - 1) * 2 * CHUNK) >> 4);
-                            const int q0 = max(qb, lo - p), q1 = min(MX_S, hi - p);
-                            uint64_t db = dBs + (uint64_t)(((q0 - 1) * CHUNK) >> 4);
-                            uint32_t dcol = tmem + (uint32_t)(p + q0 - lo) * 64;
-                            for (int q = q0; q <= q1; ++q) {
-                                tc::mma_bf16(dcol, da, db, idesc, 1u);
+                            const int q1 = min(MX_S, HI - p);
+                            uint64_t db = dBs + (uint64_t)(((qb - 1) * CHUNK) >> 4);
+                            uint32_t dcol = tmem + (uint32_t)(p + qb - LO) * 64;
+                            for (int q = qb; q <= q1; ++q) {
+                                if (e) tc::mma_bf16(dcol, da, db, idesc, 1u);
                                 db += (uint64_t)(CHUNK >> 4);
                                 dcol += 64;
                             }
                         }
-                        tc::commit(b_empty + 8 * st);
+                    } else {
+                        // one or two q per p: unrolled over the pass's (p, q)
+#pragma unroll
+                        for (int p = 1; p <= MX_S; ++p) {
+#pragma unroll
+                            for (int q = 1; q <= MX_S; ++q) {
+                                if (p + q >= LO && p + q <= HI && p >= pa && q >= qb && e)
+                                    tc::mma_bf16(tmem + (uint32_t)(p + q - LO) * 64,
+                                                 dAs + (uint64_t)(((p - 1) * 2 * CHUNK) >> 4),
+                                                 dBs + (uint64_t)(((q - 1) * CHUNK) >> 4), idesc, 1u);
+                            }
+                        }
                     }
+                    if (e) tc::commit(b_empty + 8 * st);
+                    __syncwarp();
                 }
-                tc::commit(b_accf);
+                if (ok) ok = !__any_sync(0xffffffffu, *s_err != 0);
             }
+            if (e) tc::commit(b_accf);
+            __syncwarp();
+        }
+        if (e) {
             tc::commit(b_drain);
             if (!tc::mbar_wait(b_drain, 0, WAIT_LIMIT)) atomicExch((int*)s_err, 4);
         }
+        __syncwarp();
     } else {
         // ------------------------------------------ fold + epilogue (16 warps)
         const int ew = warp - 2;
@@ -693,6 +722,27 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
 }
 
 // ------------------------------------------------------------- host side
+
+constexpr int MX_LMAX_MAIN = 2 + MAX_LEVELS - 1;   // levels 2..9 share TMEM in the main pass
+
+using GemmMixedFn = void (*)(MixedArgs);
+
+// the instance for levels lo..hi: the main pass (lo = 2, hi = 4..9) or the pass over
+// the levels above it (lo = 10, hi = 10..MIXED_LMAX)
+static GemmMixedFn gemm_mixed_kernel(int lo, int hi) {
+    if (lo == 2) {
+        switch (hi) {
+            case 4: return k_gemm_mixed<2, 4>;
+            case 5: return k_gemm_mixed<2, 5>;
+            case 6: return k_gemm_mixed<2, 6>;
+            case 7: return k_gemm_mixed<2, 7>;
+            case 8: return k_gemm_mixed<2, 8>;
+            default: return k_gemm_mixed<2, 9>;
+        }
+    }
+    return hi <= 10 ? k_gemm_mixed<10, 10> : k_gemm_mixed<10, 11>;
+}
+static_assert(MX_LMAX_MAIN == 9 && MIXED_LMAX == 11, "instances above cover levels 4..11");
 
 static uint8_t* g_zero_chunk[64] = {nullptr};
 static bool g_attr_set[64] = {false};
@@ -869,8 +919,12 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
         {
             std::lock_guard<std::mutex> lock(g_mixed_init);
             if (!g_attr_set[ctx->device]) {
-                SP_CUDA(cudaFuncSetAttribute(k_gemm_mixed,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
+                for (int h = 4; h <= MX_LMAX_MAIN; ++h)
+                    SP_CUDA(cudaFuncSetAttribute(gemm_mixed_kernel(2, h),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
+                for (int h = MX_LMAX_MAIN + 1; h <= MIXED_LMAX; ++h)
+                    SP_CUDA(cudaFuncSetAttribute(gemm_mixed_kernel(MX_LMAX_MAIN + 1, h),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
                 g_attr_set[ctx->device] = true;
             }
         }
@@ -882,7 +936,7 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
             const double per = ldexp(1.0, 18) * (top + 1 > 4 ? top + 1 : 4);
             return (int)floor((ldexp(1.0, 24) - 1.0) / per);
         };
-        const int main_hi = lmax < 2 + MAX_LEVELS - 1 ? lmax : 2 + MAX_LEVELS - 1;
+        const int main_hi = lmax < MX_LMAX_MAIN ? lmax : MX_LMAX_MAIN;
         if (lmax > main_hi) {
             MixedArgs gb = ga;
             gb.lv_lo = main_hi + 1;
@@ -891,7 +945,7 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
             gb.raw_out = 1;
             gb.add_prev = 0;
             ++ctx->launches;
-            k_gemm_mixed<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(gb);
+            gemm_mixed_kernel(gb.lv_lo, gb.lv_hi)<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(gb);
             SP_CHECK_LAUNCH();
         }
         ga.lv_lo = 2;
@@ -900,7 +954,7 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
         ga.raw_out = 0;
         ga.add_prev = lmax > main_hi ? 1 : 0;
         ++ctx->launches;
-        k_gemm_mixed<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(ga);
+        gemm_mixed_kernel(ga.lv_lo, ga.lv_hi)<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(ga);
         SP_CHECK_LAUNCH();
         cudaEventRecord(ctx->ev[EV_GEMM1], s);
         st = reduce_partials(ctx, parts, parts + 2 * nw, parts + 4 * nw, 2 * n_work);

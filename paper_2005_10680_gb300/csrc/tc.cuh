@@ -100,6 +100,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t da, uint64_t 
         : "memory");
 }
 
+// 1 in exactly one lane of a converged warp (the elected leader), 0 elsewhere
+__device__ __forceinline__ uint32_t elect_one() {
+    uint32_t e;
+    asm volatile("{ .reg .pred P; elect.sync _|P, 0xffffffff; selp.u32 %0, 1, 0, P; }" : "=r"(e));
+    return e;
+}
+
 __device__ __forceinline__ void commit(uint32_t bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
