@@ -42,8 +42,16 @@ constexpr int MX_W = 7;
 constexpr int MX_S = MX_SLICES;
 constexpr int MX_BS = 64;
 constexpr int CHUNK = 2048;                      // 64 rows x 16 K x 2 bytes
-constexpr int SLICE_BYTES = 4 * CHUNK;           // one slice of one 64 x 64 block
-constexpr int TILE_BYTES = MX_S * SLICE_BYTES;   // all slices of one block (64 KB)
+constexpr int KCH = 4;                           // K chunks of 16 in a 64-wide block
+constexpr int TILE_BYTES = MX_S * KCH * CHUNK;   // all slices of one block (72 KB)
+// Slice storage is K-chunk-major, so that the slices p..p' of one K chunk are one
+// contiguous run and reach shared memory in a single bulk copy:
+//   block tile (B operand): [K chunk][slice p][2 KB]
+//   pair tile (A operand, block rows 2I and 2I+1 of one k): [K chunk][p][half][2 KB],
+//   which is also the shared-memory order of the M = 128 operand.
+constexpr int TILE_CSTRIDE = MX_S * CHUNK;
+constexpr int PAIR_CSTRIDE = 2 * MX_S * CHUNK;
+constexpr int PAIR_BYTES = KCH * PAIR_CSTRIDE;   // 144 KB
 
 // ------------------------------------------------------------- slicing
 
@@ -99,12 +107,14 @@ __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __re
 // so x = sum_p d_p 2^(e_r - 7p) + T_9 with |d_1| <= 128, |T_9| <= 2^(e_r - 64).
 // Slice norms are exact (digit squares summed exactly per row in f32); tail norms
 // are upper bounds: |R_p| per entry, plus 1/2 where the rounding of V was inexact,
-// summed in f32 and inflated by 2^-12 to cover the f32 rounding. transpose: slice the transposed block with column
-// exponents.
+// summed in f32 and inflated by 2^-12 to cover the f32 rounding. transpose: slice the
+// transposed block with column exponents. The digits go to the block's tile (slices,
+// when given) and to its half of the pair tile (pairs, when given; transpose = 0).
 __global__ void __launch_bounds__(256)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
-        const int32_t* __restrict__ expo, uint8_t* __restrict__ slices, int8_t* __restrict__ p0,
-        double* __restrict__ sn, double* __restrict__ tn) {
+        const int32_t* __restrict__ expo, uint8_t* __restrict__ slices, uint8_t* __restrict__ pairs,
+        const int64_t* __restrict__ pair_idx, int8_t* __restrict__ p0, double* __restrict__ sn,
+        double* __restrict__ tn) {
     const int64_t s = blockIdx.x;
     const int t = threadIdx.x;
     __shared__ double T[MX_BS][MX_BS + 1];
@@ -128,7 +138,10 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
 #pragma unroll
     for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.f;
     int firstp = MX_S + 1;
-    uint8_t* out = slices + s * (int64_t)TILE_BYTES;
+    uint8_t* out = slices ? slices + s * (int64_t)TILE_BYTES : nullptr;
+    uint8_t* pout = nullptr;
+    if (pairs)
+        pout = pairs + pair_idx[(int64_t)(bi >> 1) * nb + bj] * (int64_t)PAIR_BYTES + (bi & 1) * CHUNK;
 #pragma unroll
     for (int g2 = 0; g2 < 2; ++g2) {
         const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
@@ -187,9 +200,12 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                 packed[e / 2] = (uint32_t)__bfloat16_as_ushort(b0) |
                                 ((uint32_t)__bfloat16_as_ushort(b1) << 16);
             }
-            const int off = p * SLICE_BYTES + (kg >> 1) * CHUNK + (row >> 3) * 256 + (kg & 1) * 128 +
-                            (row & 7) * 16;
-            *reinterpret_cast<uint4*>(out + off) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            const int within = (row >> 3) * 256 + (kg & 1) * 128 + (row & 7) * 16;
+            const uint4 v = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            if (out)
+                *reinterpret_cast<uint4*>(out + (kg >> 1) * TILE_CSTRIDE + p * CHUNK + within) = v;
+            if (pout)
+                *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
         }
     }
     // per-row sums -> scale by 2^(2(e_r - 7p)) (slice) or 2^(2(e_r - 63)) (tail) -> block sums
@@ -222,12 +238,16 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
 
 struct SliceSet {
     uint8_t* slices = nullptr;
+    uint8_t* pairs = nullptr;       // pair tiles (A operand)
+    int64_t* pair_idx = nullptr;    // [(nb + 1) / 2 * nb]: pair tile of (I, k), or -1
     int8_t* p0 = nullptr;
     double* sn = nullptr;
     double* tn = nullptr;
     int32_t* expo = nullptr;
     void free(cudaStream_t s) {
         dfree(slices, s);
+        dfree(pairs, s);
+        dfree(pair_idx, s);
         dfree(p0, s);
         dfree(sn, s);
         dfree(tn, s);
@@ -235,10 +255,71 @@ struct SliceSet {
     }
 };
 
-static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, SliceSet* out) {
+// pair (I, k) exists when block (2I, k) or (2I + 1, k) is stored
+__global__ void k_pair_flags(const int32_t* __restrict__ map, int nb, int32_t* __restrict__ flag) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int np = (nb + 1) / 2;
+    if (e >= (int64_t)np * nb) return;
+    const int I = (int)(e / nb), k = (int)(e % nb);
+    const int i1 = 2 * I + 1;
+    flag[e] = map[(int64_t)(2 * I) * nb + k] >= 0 || (i1 < nb && map[(int64_t)i1 * nb + k] >= 0);
+}
+
+// pair_idx from the exclusive scan of the flags (-1 where absent)
+__global__ void k_pair_index(const int32_t* __restrict__ flag, int64_t* __restrict__ idx, int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n && !flag[e]) idx[e] = -1;
+}
+
+// zero the half of every pair tile whose block is not stored (one CTA per (I, k))
+__global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb,
+                                    const int64_t* __restrict__ idx, uint8_t* __restrict__ pairs) {
+    const int64_t e = blockIdx.x;
+    const int I = (int)(e / nb), k = (int)(e % nb);
+    const int64_t pi = idx[e];
+    if (pi < 0) return;
+    for (int half = 0; half < 2; ++half) {
+        const int i = 2 * I + half;
+        if (i < nb && map[(int64_t)i * nb + k] >= 0) continue;
+        uint8_t* base = pairs + pi * (int64_t)PAIR_BYTES + half * CHUNK;
+        for (int o = threadIdx.x; o < KCH * MX_S * (CHUNK / 16); o += blockDim.x) {
+            const int ch = o / (CHUNK / 16), w = o % (CHUNK / 16);   // ch: (K chunk, slice)
+            *reinterpret_cast<uint4*>(base + (int64_t)ch * 2 * CHUNK + w * 16) = make_uint4(0, 0, 0, 0);
+        }
+    }
+}
+
+// Slices of X: block tiles when want_tiles, pair tiles when want_pairs (transpose = 0).
+static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, int want_tiles,
+                        int want_pairs, SliceSet* out) {
     cudaStream_t s = ctx->stream;
     const int64_t ns = X->nslots > 0 ? X->nslots : 1;
-    SP_TRY(dalloc((void**)&out->slices, (size_t)ns * TILE_BYTES, s));
+    if (want_tiles) SP_TRY(dalloc((void**)&out->slices, (size_t)ns * TILE_BYTES, s));
+    if (want_pairs) {
+        const int nb = X->nb;
+        const int64_t ne = (int64_t)((nb + 1) / 2) * nb;
+        int32_t* flag = nullptr;
+        unsigned long long* tot = nullptr;
+        SP_TRY(dalloc((void**)&flag, sizeof(int32_t) * ne, s));
+        SP_TRY(dalloc((void**)&out->pair_idx, sizeof(int64_t) * (ne + 1), s));
+        SP_TRY(dalloc((void**)&tot, 8, s));
+        const unsigned g = (unsigned)((ne + 255) / 256);
+        ++ctx->launches;
+        k_pair_flags<<<g, 256, 0, s>>>(X->d_map, nb, flag);
+        SP_TRY(scan_i32_to_i64(ctx, flag, out->pair_idx, ne, tot));
+        ++ctx->launches;
+        k_pair_index<<<g, 256, 0, s>>>(flag, out->pair_idx, ne);
+        unsigned long long npairs = 0;
+        SP_CUDA(cudaMemcpyAsync(&npairs, tot, 8, cudaMemcpyDeviceToHost, s));
+        SP_CUDA(cudaStreamSynchronize(s));
+        dfree(flag, s);
+        dfree(tot, s);
+        SP_TRY(dalloc((void**)&out->pairs, (size_t)(npairs > 0 ? npairs : 1) * PAIR_BYTES, s));
+        if (npairs > 0) {
+            ++ctx->launches;
+            k_pair_zero_missing<<<(unsigned)ne, 256, 0, s>>>(X->d_map, nb, out->pair_idx, out->pairs);
+        }
+    }
     SP_TRY(dalloc((void**)&out->p0, (size_t)ns, s));
     SP_TRY(dalloc((void**)&out->sn, sizeof(double) * ns * MX_S, s));
     SP_TRY(dalloc((void**)&out->tn, sizeof(double) * ns * MX_S, s));
@@ -257,8 +338,8 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
     if (X->nslots > 0) {
         ++ctx->launches;
         k_split<<<(unsigned)X->nslots, 256, 0, s>>>(X->d_tiles, X->d_coord, X->nb, transpose,
-                                                    out->expo, out->slices, out->p0, out->sn,
-                                                    out->tn);
+                                                    out->expo, out->slices, out->pairs,
+                                                    out->pair_idx, out->p0, out->sn, out->tn);
     }
     SP_CHECK_LAUNCH();
     dfree(rmax, s);
@@ -268,7 +349,9 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
 // ------------------------------------------------------------ planning
 
 // Work item: a pair of block rows {2I, 2I+1} times block column j (M = 128).
-// Task: (slot of A_{2I,k} or -1, slot of A_{2I+1,k} or -1, slot of the B operand).
+// Task: (slot of A_{2I,k} or -1, slot of A_{2I+1,k} or -1, slot of the B operand,
+// 2 * pair tile of (I, k) + w), where w = 1 when the pair tile can be copied whole:
+// each half is either kept or not stored at all (its part of the tile is zero).
 __device__ __forceinline__ bool mx_keep(const ChargeData& ch, int i, int k, int j, double tau,
                                         int32_t* sa, int32_t* sb) {
     const int nb = ch.nb;
@@ -342,6 +425,7 @@ __global__ void k_pair_fill(ChargeData ch, Raster rs, const int32_t* __restrict_
                             int32_t* __restrict__ work_ij, int32_t* __restrict__ work_out,
                             int64_t* __restrict__ work_off, int32_t* __restrict__ task,
                             const int8_t* __restrict__ p0A, const int8_t* __restrict__ p0B,
+                            const int64_t* __restrict__ pair_idx,
                             unsigned long long* __restrict__ counters) {
     const int nb = ch.nb;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -362,14 +446,16 @@ __global__ void k_pair_fill(ChargeData ch, Raster rs, const int32_t* __restrict_
         work_off[w] = t;
         const double tau = *d_tau;
         for (int k = 0; k < nb; ++k) {
-            int32_t sa0, sb0, sa1 = -1, sb1;
+            int32_t sa0, sb0, sa1 = -1, sb1 = -1;
             bool kt = mx_keep(ch, i0, k, j, tau, &sa0, &sb0);
             bool kb = (i1 < nb) && mx_keep(ch, i1, k, j, tau, &sa1, &sb1);
             if (!(kt || kb)) continue;
             const int32_t s0 = kt ? sa0 : -1, s1 = kb ? sa1 : -1, sb = kt ? sb0 : sb1;
-            task[3 * t + 0] = s0;
-            task[3 * t + 1] = s1;
-            task[3 * t + 2] = sb;
+            const bool whole = (kt || sa0 < 0) && (kb || i1 >= nb || sa1 < 0);
+            task[4 * t + 0] = s0;
+            task[4 * t + 1] = s1;
+            task[4 * t + 2] = sb;
+            task[4 * t + 3] = (int32_t)(2 * pair_idx[(int64_t)I * nb + k] + (whole ? 1 : 0));
             formed += (kt ? 1 : 0) + (kb ? 1 : 0);
             const int pa = min(s0 >= 0 ? (int)p0A[s0] : MX_S + 1, s1 >= 0 ? (int)p0A[s1] : MX_S + 1);
             pairs += n_level_pairs(pa, p0B[sb], ch.lmax);
@@ -402,14 +488,14 @@ constexpr int MAX_LEVELS = 8;               // 8 x 64 = all 512 TMEM columns
 constexpr long long WAIT_LIMIT = 1ll << 22;
 
 struct MixedArgs {
-    const uint8_t* slA;
-    const uint8_t* slB;
+    const uint8_t* pairA;        // pair tiles of A
+    const uint8_t* slB;          // block tiles of the B operand
     const int8_t* p0A;
     const int8_t* p0B;
     const int32_t* expA;
     const int32_t* expB;
     const uint8_t* zero_chunk;   // CHUNK bytes of zeros
-    const int32_t* task;         // [3 * n_tasks]
+    const int32_t* task;         // [4 * n_tasks]
     const int32_t* work_ij;
     const int32_t* work_out;     // [4 * n_work]
     const int64_t* work_off;
@@ -478,12 +564,13 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
         bool ok = true;
         for (int64_t base = t0; base < t1 && ok; base += 32) {
             const int64_t tl = base + lane;
-            int32_t s0 = -1, s1 = -1, sb = 0;
+            int32_t s0 = -1, s1 = -1, sb = 0, pw = 0;
             int pa = MX_S + 1, qb = MX_S + 1;
             if (tl < t1) {
-                s0 = a.task[3 * tl];
-                s1 = a.task[3 * tl + 1];
-                sb = a.task[3 * tl + 2];
+                s0 = a.task[4 * tl];
+                s1 = a.task[4 * tl + 1];
+                sb = a.task[4 * tl + 2];
+                pw = a.task[4 * tl + 3];
                 pa = min(tile_p0(a.p0A, s0), tile_p0(a.p0A, s1));
                 qb = tile_p0(a.p0B, sb);
             }
@@ -492,6 +579,9 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                 const int32_t js0 = __shfl_sync(0xffffffffu, s0, j);
                 const int32_t js1 = __shfl_sync(0xffffffffu, s1, j);
                 const int32_t jsb = __shfl_sync(0xffffffffu, sb, j);
+                const int32_t jpw = __shfl_sync(0xffffffffu, pw, j);
+                const uint8_t* pt = a.pairA + (int64_t)(jpw >> 1) * PAIR_BYTES;
+                const uint8_t* bt = a.slB + (int64_t)jsb * TILE_BYTES;
                 const int jpa = __shfl_sync(0xffffffffu, pa, j);
                 const int jqb = __shfl_sync(0xffffffffu, qb, j);
                 const int pmax = min(MX_S, hi - jqb), qmax = min(MX_S, hi - jpa);
@@ -513,19 +603,24 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                     if (!ok) break;
                     const uint32_t sA = tc::smem_u32(stages + st * STAGE_BYTES);
                     const uint32_t sB = sA + STAGE_A;
-                    if (lane < 2 * np) {
+                    // A: slices jpa..pmax of both halves, one run of the pair tile; when a
+                    // stored half is not kept, per-slice copies with zeros for that half
+                    if (jpw & 1) {
+                        if (lane == 0 && np > 0)
+                            tc::bulk_g2s(sA + (jpa - 1) * 2 * CHUNK,
+                                         pt + c * PAIR_CSTRIDE + (jpa - 1) * 2 * CHUNK,
+                                         (uint32_t)np * 2 * CHUNK, b_full + 8 * st);
+                    } else if (lane < 2 * np) {
                         const int p = jpa + (lane >> 1), half = lane & 1;
                         const int32_t sl = half ? js1 : js0;
-                        const uint8_t* g = sl >= 0 ? a.slA + (int64_t)sl * TILE_BYTES +
-                                                         (p - 1) * SLICE_BYTES + c * CHUNK
+                        const uint8_t* g = sl >= 0 ? pt + c * PAIR_CSTRIDE + (p - 1) * 2 * CHUNK + half * CHUNK
                                                    : a.zero_chunk;
                         tc::bulk_g2s(sA + (p - 1) * 2 * CHUNK + half * CHUNK, g, CHUNK, b_full + 8 * st);
-                    } else if (lane < 2 * np + nq) {
-                        const int q = jqb + (lane - 2 * np);
-                        tc::bulk_g2s(sB + (q - 1) * CHUNK,
-                                     a.slB + (int64_t)jsb * TILE_BYTES + (q - 1) * SLICE_BYTES + c * CHUNK,
-                                     CHUNK, b_full + 8 * st);
                     }
+                    // B: slices jqb..qmax, one run of the block tile
+                    if (lane == 31 && nq > 0)
+                        tc::bulk_g2s(sB + (jqb - 1) * CHUNK, bt + c * TILE_CSTRIDE + (jqb - 1) * CHUNK,
+                                     (uint32_t)nq * CHUNK, b_full + 8 * st);
                 }
             }
         }
@@ -770,8 +865,9 @@ int mixed_prepare(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, int sy
     }
     SliceSet* sa = new SliceSet();
     SliceSet* sb = sym ? sa : new SliceSet();
-    SP_TRY(split_matrix(ctx, A, 0, sa));
-    if (!sym) SP_TRY(split_matrix(ctx, B, 1, sb));
+    // A needs pair tiles; the B operand block tiles (for symmetric X, of X itself)
+    SP_TRY(split_matrix(ctx, A, 0, sym ? 1 : 0, 1, sa));
+    if (!sym) SP_TRY(split_matrix(ctx, B, 1, 1, 0, sb));
     mp->sa = sa;
     mp->sb = sb;
     mp->sym = sym;
@@ -882,12 +978,12 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     SP_TRY(dalloc((void**)&work_ij, sizeof(int32_t) * nw, s));
     SP_TRY(dalloc((void**)&work_out, sizeof(int32_t) * 4 * nw, s));
     SP_TRY(dalloc((void**)&work_off, sizeof(int64_t) * (nw + 1), s));
-    SP_TRY(dalloc((void**)&task, sizeof(int32_t) * 3 * (n_pt > 0 ? n_pt : 1), s));
+    SP_TRY(dalloc((void**)&task, sizeof(int32_t) * 4 * (n_pt > 0 ? n_pt : 1), s));
     SP_TRY(dalloc((void**)&parts, sizeof(double) * 6 * nw, s));
     SP_CUDA(cudaMemsetAsync(&sc->mx_formed, 0, 2 * sizeof(unsigned long long), s));
     ++ctx->launches;
     k_pair_fill<<<G, 256, 0, s>>>(ch, rs, of, oidx, sym, d_tau, pwf, pwidx, ptoff, work_ij, work_out,
-                                  work_off, task, sa->p0, sbs->p0, &sc->mx_formed);
+                                  work_off, task, sa->p0, sbs->p0, sa->pair_idx, &sc->mx_formed);
     ++ctx->launches;
     k_last_off<<<1, 1, 0, s>>>(work_off, n_work, ptoff, npb);
     SP_CHECK_LAUNCH();
@@ -895,7 +991,7 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     if (n_work > 0) {
         MixedArgs ga;
         memset(&ga, 0, sizeof ga);
-        ga.slA = sa->slices;
+        ga.pairA = sa->pairs;
         ga.slB = sbs->slices;
         ga.p0A = sa->p0;
         ga.p0B = sbs->p0;
