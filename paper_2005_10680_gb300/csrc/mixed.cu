@@ -110,7 +110,7 @@ __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __re
 // summed in f32 and inflated by 2^-12 to cover the f32 rounding. transpose: slice the
 // transposed block with column exponents. The digits go to the block's tile (slices,
 // when given) and to its half of the pair tile (pairs, when given; transpose = 0).
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
         const int32_t* __restrict__ expo, uint8_t* __restrict__ slices, uint8_t* __restrict__ pairs,
         const int64_t* __restrict__ pair_idx, int8_t* __restrict__ p0, double* __restrict__ sn,
@@ -145,7 +145,9 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
 #pragma unroll
     for (int g2 = 0; g2 < 2; ++g2) {
         const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
-        int dig[8][MX_S];
+        uint32_t pk[MX_S][4];                      // bf16 pairs of the 8 values, per slice
+#pragma unroll
+        for (int p = 0; p < MX_S; ++p) pk[p][0] = pk[p][1] = pk[p][2] = pk[p][3] = 0u;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             // exact fixed point V = round(x 2^(63 - e_r)) from the bits of x
@@ -175,33 +177,26 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             const float half = inexact ? 0.5f : 0.f;
             long long rem = V;                     // digits from the bottom
 #pragma unroll
-            for (int p = MX_S - 1; p >= 1; --p) {
-                const long long d = ((rem + 64) & 127) - 64;
-                dig[e][p] = (int)d;
-                rem = (rem - d) >> 7;
-                // tail after digit p (in units of 2^(e_r - 63)): V - rem 2^(7(S - p))
-                const long long Rp = V - rem * (1ll << (MX_W * (MX_S - p)));
-                const float rf = fabsf((float)Rp) + half;
-                sr[p - 1] = fmaf(rf, rf, sr[p - 1]);
+            for (int p = MX_S - 1; p >= 0; --p) {
+                const int d = p > 0 ? (int)(((rem + 64) & 127) - 64) : (int)rem;
+                if (p > 0) {
+                    rem = (rem - d) >> 7;
+                    // tail after digit p (in units of 2^(e_r - 63)): V - rem 2^(7(S - p))
+                    const long long Rp = V - rem * (1ll << (MX_W * (MX_S - p)));
+                    const float rf = fabsf((float)Rp) + half;
+                    sr[p - 1] = fmaf(rf, rf, sr[p - 1]);
+                }
+                sa[p] = fmaf((float)d, (float)d, sa[p]);
+                if (d != 0 && p + 1 < firstp) firstp = p + 1;
+                pk[p][e >> 1] |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)d))
+                                 << (16 * (e & 1));
             }
-            dig[e][0] = (int)rem;
             sr[MX_S - 1] += half * half;           // tail after all digits: |T_S| <= 1/2 unit
         }
 #pragma unroll
         for (int p = 0; p < MX_S; ++p) {
-            uint32_t packed[4];
-#pragma unroll
-            for (int e = 0; e < 8; e += 2) {
-                const int a0 = dig[e][p], a1 = dig[e + 1][p];
-                sa[p] += (float)(a0 * a0 + a1 * a1);
-                if ((a0 | a1) != 0 && p + 1 < firstp) firstp = p + 1;
-                const __nv_bfloat16 b0 = __float2bfloat16_rn((float)a0);
-                const __nv_bfloat16 b1 = __float2bfloat16_rn((float)a1);
-                packed[e / 2] = (uint32_t)__bfloat16_as_ushort(b0) |
-                                ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-            }
             const int within = (row >> 3) * 256 + (kg & 1) * 128 + (row & 7) * 16;
-            const uint4 v = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+            const uint4 v = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
             if (out)
                 *reinterpret_cast<uint4*>(out + (kg >> 1) * TILE_CSTRIDE + p * CHUNK + within) = v;
             if (pout)
@@ -718,6 +713,8 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                 break;
             }
             tc::fence_after();
+            // each exact level sum g (|g| < 2^24, converted in int32) enters V with
+            // weight 2^sh, sh = 7 (hi - lv)
             for (int lv = lo; lv <= hi; ++lv) {
                 uint32_t v[16];
                 tc::tmem_ld16(trow + (uint32_t)(lv - lo) * 64, v);
