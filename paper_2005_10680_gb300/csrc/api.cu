@@ -105,6 +105,29 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         } else {
             int lo = 4, hi = MIXED_LMAX;
             double ec_hi = -1.0;
+            // start from the previous step's level count and its neighbour below;
+            // the charge is non-increasing in L, so the bisection that follows
+            // returns the same L as without this start
+            const int hl = ctx->hint_lmax;
+            if (hl >= lo && hl < hi) {
+                double ec = 0.0;
+                st = charge_at(hl, &ec);
+                if (st == SPAMM_OK && ec <= 0.5 * delta) {
+                    hi = hl;
+                    ec_hi = ec;
+                    if (hl - 1 >= lo) {
+                        st = charge_at(hl - 1, &ec);
+                        if (st == SPAMM_OK && ec <= 0.5 * delta) {
+                            hi = hl - 1;
+                            ec_hi = ec;
+                        } else if (st == SPAMM_OK) {
+                            lo = hl;
+                        }
+                    }
+                } else if (st == SPAMM_OK) {
+                    lo = hl + 1;
+                }
+            }
             while (lo < hi && st == SPAMM_OK) {
                 const int mid = (lo + hi) / 2;
                 double ec = 0.0;
@@ -137,7 +160,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         ChargeData ch = use_mixed ? mixed_charge(A, B, nA, nB, mp, lmax_used) : ChargeData();
         int ev2 = 0;
         if (search) {
-            st = cse_search(ctx, A, nA, nB, delta, ch, &ev2);
+            st = cse_search(ctx, A, nA, nB, delta, ch, &ev2, ctx->hint_tau);
             ++ctx->launches;
             k_select_tau<<<1, 1, 0, s>>>(sc, ctx->d_tau, SPAMM_N_TAU);
         } else {
@@ -204,6 +227,8 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     r.bound = (search && h.hi >= SPAMM_N_TAU) ? 0.0 : h.err_at_hi;
     r.bound_round = use_mixed ? err_charge : 0.0;
     r.lmax = use_mixed ? lmax_used : 0;
+    if (search) ctx->hint_tau = h.hi < SPAMM_N_TAU ? h.hi : SPAMM_N_TAU - 1;
+    if (use_mixed && search) ctx->hint_lmax = lmax_used;
     r.candidates = n_cand;
     r.kept = n_kept;
     r.formed = use_mixed ? (int64_t)h.mx_formed : n_tasks;

@@ -46,6 +46,11 @@ struct spamm_ctx {
     unsigned long long launches;  // kernels launched through this context
     int refs;                     // matrices allocated through this context and not yet freed
     int closed;                   // spamm_destroy was called; freed when refs reaches 0
+    // starting points for the next searches on this context (the last selected tau
+    // index and slice level count); the searches return the same answer from any
+    // start, since the bound is monotone along both
+    int hint_tau = -1;
+    int hint_lmax = 0;
 };
 
 struct spamm_mat {
@@ -174,7 +179,7 @@ int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double*
              const double* d_tau_ptr, double* d_err, const ChargeData& ch);
 // bisection for the tau index; fills DevScalars lo/hi/err_at_hi
 int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
-               double delta, const ChargeData& ch, int* evals);
+               double delta, const ChargeData& ch, int* evals, int hint = -1);
 // out[i,j] = in[min(i,j), max(i,j)]: a bitwise-symmetric copy of a norm map
 int sym_norms(spamm_ctx* ctx, const double* in, int nb, double* out);
 

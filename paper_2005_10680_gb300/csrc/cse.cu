@@ -190,8 +190,26 @@ __global__ void k_bisect_step(DevScalars* sc, const double* __restrict__ tau, do
     }
 }
 
+__global__ void k_set_tau_index(DevScalars* sc, const double* __restrict__ tau, int k) {
+    sc->tau_mid = tau[k];
+    sc->done = 0;
+}
+
+__global__ void k_set_search(DevScalars* sc, int hi, double err_at_hi) {
+    sc->hi = hi;
+    sc->lo = hi;
+    sc->err_at_hi = err_at_hi;
+    sc->done = 1;
+}
+
+// Smallest table index k with E[k] < delta (N when there is none). Without a hint:
+// bisection on the device (ceil(log2(N + 1)) evaluations, no host round trip). With a
+// hint (the previous selection): the hint and its neighbours first, widening the
+// bracket by doubling, then bisection inside it. E is non-increasing in k (fewer
+// skipped products, each leaf term min(p, c) <= p, sums of nonnegative terms in a
+// fixed order), so both return the same index.
 int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
-               double delta, const ChargeData& d_charge, int* evals) {
+               double delta, const ChargeData& d_charge, int* evals, int hint) {
     cudaStream_t s = ctx->stream;
     DevScalars* sc = (DevScalars*)ctx->d_scalars;
     size_t e = level_buf_elems(A);
@@ -199,6 +217,75 @@ int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const doubl
     SP_TRY(dalloc((void**)&b0, sizeof(double) * e, s));
     SP_TRY(dalloc((void**)&b1, sizeof(double) * e, s));
     const int N = SPAMM_N_TAU;
+    if (hint >= 0 && hint < N) {
+        int n_ev = 0;
+        int st = SPAMM_OK;
+        auto E = [&](int k, double* out) -> int {
+            ++ctx->launches;
+            k_set_tau_index<<<1, 1, 0, s>>>(sc, ctx->d_tau, k);
+            int r = cse_eval_impl(ctx, A, nA, nB, &sc->tau_mid, &sc->done, &sc->err_mid, d_charge,
+                                  b0, b1);
+            if (r != SPAMM_OK) return r;
+            if (cudaMemcpyAsync(out, &sc->err_mid, sizeof(double), cudaMemcpyDeviceToHost, s) !=
+                    cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return SPAMM_ECUDA;
+            ++n_ev;
+            return SPAMM_OK;
+        };
+        int lo = 0, hi = N;     // the answer lies in [lo, hi]; E[hi] < delta unless hi == N
+        double ehi = 0.0, ex = 0.0;
+        st = E(hint, &ex);
+        if (st == SPAMM_OK && ex < delta) {
+            hi = hint;
+            ehi = ex;
+            for (int step = 1; hi > lo && st == SPAMM_OK; step *= 2) {
+                const int x = hi - step > lo ? hi - step : lo;
+                st = E(x, &ex);
+                if (st != SPAMM_OK) break;
+                if (ex < delta) {
+                    hi = x;
+                    ehi = ex;
+                } else {
+                    lo = x + 1;
+                    break;
+                }
+            }
+        } else if (st == SPAMM_OK) {
+            lo = hint + 1;
+            for (int step = 1; lo < hi && st == SPAMM_OK; step *= 2) {
+                const int x = lo + step - 1 < hi - 1 ? lo + step - 1 : hi - 1;
+                st = E(x, &ex);
+                if (st != SPAMM_OK) break;
+                if (ex < delta) {
+                    hi = x;
+                    ehi = ex;
+                    break;
+                }
+                lo = x + 1;
+            }
+        }
+        while (lo < hi && st == SPAMM_OK) {
+            const int mid = (lo + hi) / 2;
+            st = E(mid, &ex);
+            if (st != SPAMM_OK) break;
+            if (ex < delta) {
+                hi = mid;
+                ehi = ex;
+            } else {
+                lo = mid + 1;
+            }
+        }
+        if (st == SPAMM_OK) {
+            ++ctx->launches;
+            k_set_search<<<1, 1, 0, s>>>(sc, hi, ehi);
+            st = cudaGetLastError() == cudaSuccess ? SPAMM_OK : SPAMM_ECUDA;
+        }
+        dfree(b0, s);
+        dfree(b1, s);
+        if (evals) *evals = n_ev;
+        return st;
+    }
     int steps = 0;
     while ((1 << steps) < N + 1) ++steps;
     ++ctx->launches;
