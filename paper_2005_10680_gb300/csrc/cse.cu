@@ -85,10 +85,19 @@ __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restri
                     v = p;
                 } else if (ch.lmax > 0) {
                     // kept: the mixed-precision product's error, or the whole product
-                    // when the charge is not below it (then it is not formed)
-                    const int32_t sa = ch.mapA[(int64_t)i * nb + k];
-                    const int32_t sb = charge_bslot(ch, k, j);
-                    v = fmin(p, charge(ch, sa, sb, nB[(int64_t)k * nb + j]));
+                    // when the charge is not below it (then it is not formed). A
+                    // symmetric SP2 step writes block (i, j) below the diagonal as the
+                    // transpose of block (j, i), whose products are (j, k, i): charge
+                    // those. Blocks of the diagonal pair of block rows (i/2 == j/2) are
+                    // formed directly, from their own products.
+                    int ii = i, jj = j;
+                    if (ch.bt_from_a && (i >> 1) > (j >> 1)) {
+                        ii = j;
+                        jj = i;
+                    }
+                    const int32_t sa = ch.mapA[(int64_t)ii * nb + k];
+                    const int32_t sb = charge_bslot(ch, k, jj);
+                    v = fmin(p, charge(ch, sa, sb, nB[(int64_t)k * nb + jj]));
                 }
             }
         }
