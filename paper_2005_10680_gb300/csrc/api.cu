@@ -232,7 +232,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     r.candidates = n_cand;
     r.kept = n_kept;
     r.formed = use_mixed ? (int64_t)h.mx_formed : n_tasks;
-    r.pipe_flops = use_mixed ? (double)h.mx_pairs * 2.0 * 128 * 64 * 64
+    r.pipe_flops = use_mixed ? (double)h.mx_pairs * 2.0 * 128 * 128 * 64
                              : 2.0 * A->bs * A->bs * A->bs * (double)n_tasks;
     r.nnzb_out = C->nnzb;
     r.fro_out = std::sqrt(h.fro2);

@@ -93,8 +93,8 @@ struct DevScalars {
     // reductions (fro2, trace, idem2 must stay adjacent)
     double fro2, trace, idem2, bound_round2;
     double err_charge;               // Algorithm 3 bound with tau = 0 (mixed charges only)
-    unsigned long long mx_formed;    // mixed: leaf products formed (block halves of pair tasks)
-    unsigned long long mx_pairs;     // mixed: (p, q) slice pairs issued (4 MMAs of 128x64x16 each)
+    unsigned long long mx_formed;    // mixed: leaf products formed
+    unsigned long long mx_pairs;     // mixed: (p, q) slice pairs of tile tasks (4 MMAs of 128x128x16)
     // truncation
     unsigned long long trunc_removed;
     double trunc_removed_sq;

@@ -81,15 +81,24 @@ __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restri
             const double tau = *d_tau;
             const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
             if (p != 0.0) {
-                if (p < tau) {
-                    v = p;
-                } else if (ch.lmax > 0) {
-                    // kept: the mixed-precision product's error, or the whole product
-                    // when the charge is not below it (then it is not formed). A
-                    // symmetric SP2 step writes block (i, j) below the diagonal as the
-                    // transpose of block (j, i), whose products are (j, k, i): charge
-                    // those. Blocks of the diagonal pair of block rows (i/2 == j/2) are
-                    // formed directly, from their own products.
+                if (ch.lmax == 0) {
+                    // float64 leaf products: Algorithm 3's leaf, p if skipped
+                    v = p < tau ? p : 0.0;
+                } else {
+                    // mixed form: the leaf-product kernel forms every stored product of
+                    // a 2 x 2 block tile at k once some product of the tile reaches
+                    // tau (its trigger: the largest one, the product of the pair
+                    // maxima). A formed product is charged its slicing charge c, a
+                    // skipped one max(p, c): its error is at most p, and the max keeps
+                    // the bound non-increasing as tau decreases. A symmetric SP2 step
+                    // writes the blocks below the diagonal tiles as transposes of
+                    // blocks (j, i), whose products are (j, k, i): charge those.
+                    const int i0 = i & ~1, j0 = j & ~1;
+                    const double ra = fmax(nA[(int64_t)i0 * nb + k],
+                                           i0 + 1 < nb ? nA[(int64_t)(i0 + 1) * nb + k] : 0.0);
+                    const double rb = fmax(nB[(int64_t)k * nb + j0],
+                                           j0 + 1 < nb ? nB[(int64_t)k * nb + j0 + 1] : 0.0);
+                    const double m = ra * rb;
                     int ii = i, jj = j;
                     if (ch.bt_from_a && (i >> 1) > (j >> 1)) {
                         ii = j;
@@ -97,7 +106,8 @@ __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restri
                     }
                     const int32_t sa = ch.mapA[(int64_t)ii * nb + k];
                     const int32_t sb = charge_bslot(ch, k, jj);
-                    v = fmin(p, charge(ch, sa, sb, nB[(int64_t)k * nb + jj]));
+                    const double c = charge(ch, sa, sb, nB[(int64_t)k * nb + jj]);
+                    v = m >= tau ? c : fmax(p, c);
                 }
             }
         }

@@ -109,7 +109,7 @@ __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __re
 // are upper bounds: |R_p| per entry, plus 1/2 where the rounding of V was inexact,
 // summed in f32 and inflated by 2^-12 to cover the f32 rounding. transpose: slice the
 // transposed block with column exponents. The digits go to the block's tile (slices,
-// when given) and to its half of the pair tile (pairs, when given; transpose = 0).
+// when given) and to its half of the pair tile (pairs, when given).
 __global__ void __launch_bounds__(256, 3)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
         const int32_t* __restrict__ expo, uint8_t* __restrict__ slices, uint8_t* __restrict__ pairs,
@@ -140,8 +140,11 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
     int firstp = MX_S + 1;
     uint8_t* out = slices ? slices + s * (int64_t)TILE_BYTES : nullptr;
     uint8_t* pout = nullptr;
-    if (pairs)
-        pout = pairs + pair_idx[(int64_t)(bi >> 1) * nb + bj] * (int64_t)PAIR_BYTES + (bi & 1) * CHUNK;
+    if (pairs) {
+        // pairing along block rows (transpose = 0) or block columns (transpose = 1)
+        const int r = transpose ? bj : bi, k = transpose ? bi : bj;
+        pout = pairs + pair_idx[(int64_t)(r >> 1) * nb + k] * (int64_t)PAIR_BYTES + (r & 1) * CHUNK;
+    }
 #pragma unroll
     for (int g2 = 0; g2 < 2; ++g2) {
         const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
@@ -250,14 +253,22 @@ struct SliceSet {
     }
 };
 
-// pair (I, k) exists when block (2I, k) or (2I + 1, k) is stored
-__global__ void k_pair_flags(const int32_t* __restrict__ map, int nb, int32_t* __restrict__ flag) {
+// block (2I + h, k) of the pairing: rows of X, or columns of X when transpose
+__device__ __forceinline__ int32_t pair_block(const int32_t* map, int nb, int transpose, int r,
+                                              int k) {
+    if (r >= nb) return -1;
+    return transpose ? map[(int64_t)k * nb + r] : map[(int64_t)r * nb + k];
+}
+
+// pair (I, k) exists when block (2I, k) or (2I + 1, k) of the pairing is stored
+__global__ void k_pair_flags(const int32_t* __restrict__ map, int nb, int transpose,
+                             int32_t* __restrict__ flag) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int np = (nb + 1) / 2;
     if (e >= (int64_t)np * nb) return;
     const int I = (int)(e / nb), k = (int)(e % nb);
-    const int i1 = 2 * I + 1;
-    flag[e] = map[(int64_t)(2 * I) * nb + k] >= 0 || (i1 < nb && map[(int64_t)i1 * nb + k] >= 0);
+    flag[e] = pair_block(map, nb, transpose, 2 * I, k) >= 0 ||
+              pair_block(map, nb, transpose, 2 * I + 1, k) >= 0;
 }
 
 // pair_idx from the exclusive scan of the flags (-1 where absent)
@@ -267,15 +278,14 @@ __global__ void k_pair_index(const int32_t* __restrict__ flag, int64_t* __restri
 }
 
 // zero the half of every pair tile whose block is not stored (one CTA per (I, k))
-__global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb,
+__global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb, int transpose,
                                     const int64_t* __restrict__ idx, uint8_t* __restrict__ pairs) {
     const int64_t e = blockIdx.x;
     const int I = (int)(e / nb), k = (int)(e % nb);
     const int64_t pi = idx[e];
     if (pi < 0) return;
     for (int half = 0; half < 2; ++half) {
-        const int i = 2 * I + half;
-        if (i < nb && map[(int64_t)i * nb + k] >= 0) continue;
+        if (pair_block(map, nb, transpose, 2 * I + half, k) >= 0) continue;
         uint8_t* base = pairs + pi * (int64_t)PAIR_BYTES + half * CHUNK;
         for (int o = threadIdx.x; o < KCH * MX_S * (CHUNK / 16); o += blockDim.x) {
             const int ch = o / (CHUNK / 16), w = o % (CHUNK / 16);   // ch: (K chunk, slice)
@@ -284,7 +294,8 @@ __global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb,
     }
 }
 
-// Slices of X: block tiles when want_tiles, pair tiles when want_pairs (transpose = 0).
+// Slices of X: block tiles when want_tiles, pair tiles when want_pairs (pairs of block
+// rows, or of block columns when transpose).
 static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, int want_tiles,
                         int want_pairs, SliceSet* out) {
     cudaStream_t s = ctx->stream;
@@ -300,7 +311,7 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, int w
         SP_TRY(dalloc((void**)&tot, 8, s));
         const unsigned g = (unsigned)((ne + 255) / 256);
         ++ctx->launches;
-        k_pair_flags<<<g, 256, 0, s>>>(X->d_map, nb, flag);
+        k_pair_flags<<<g, 256, 0, s>>>(X->d_map, nb, transpose, flag);
         SP_TRY(scan_i32_to_i64(ctx, flag, out->pair_idx, ne, tot));
         ++ctx->launches;
         k_pair_index<<<g, 256, 0, s>>>(flag, out->pair_idx, ne);
@@ -312,7 +323,8 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, int w
         SP_TRY(dalloc((void**)&out->pairs, (size_t)(npairs > 0 ? npairs : 1) * PAIR_BYTES, s));
         if (npairs > 0) {
             ++ctx->launches;
-            k_pair_zero_missing<<<(unsigned)ne, 256, 0, s>>>(X->d_map, nb, out->pair_idx, out->pairs);
+            k_pair_zero_missing<<<(unsigned)ne, 256, 0, s>>>(X->d_map, nb, transpose, out->pair_idx,
+                                                             out->pairs);
         }
     }
     SP_TRY(dalloc((void**)&out->p0, (size_t)ns, s));
@@ -343,68 +355,58 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, int w
 
 // ------------------------------------------------------------ planning
 
-// Work item: a pair of block rows {2I, 2I+1} times block column j (M = 128).
-// Task: (slot of A_{2I,k} or -1, slot of A_{2I+1,k} or -1, slot of the B operand,
-// 2 * pair tile of (I, k) + w), where w = 1 when the pair tile can be copied whole:
-// each half is either kept or not stored at all (its part of the tile is zero).
-__device__ __forceinline__ bool mx_keep(const ChargeData& ch, int i, int k, int j, double tau,
-                                        int32_t* sa, int32_t* sb) {
-    const int nb = ch.nb;
-    *sa = ch.mapA[(int64_t)i * nb + k];
-    *sb = ch.bt_from_a ? ch.mapA[(int64_t)j * nb + k] : ch.mapB[(int64_t)k * nb + j];
-    const int32_t pb = ch.bt_from_a ? *sb : ch.mapB[(int64_t)k * nb + j];
-    if (*sa < 0 || pb < 0) return false;
-    const double p = ch.nA[(int64_t)i * nb + k] * ch.nB[(int64_t)k * nb + j];
-    if (p < tau) return false;
-    return charge(ch, *sa, *sb, ch.nB[(int64_t)k * nb + j]) < p;
-}
+// Work item: tile (I, J) = block rows {2I, 2I+1} x block columns {2J, 2J+1}
+// (M = N = 128). For each k whose tile trigger holds, i.e. the largest norm product
+// max(n_{2I,k}, n_{2I+1,k}) max(n_{k,2J}, n_{k,2J+1}) is >= tau, every product
+// A_{2I+h,k} B_{k,2J+c} of the tile whose blocks are stored is formed. The bound
+// charges each formed product its slicing charge and each other one its norm
+// product (Algorithm 3's leaf rule in cse.cu). A symmetric SP2 step takes the tiles
+// I <= J; for I < J the tile's four blocks are also written transposed.
+// Task: (pair tile of A at (I, k), pair tile of the B operand at (J, k), pa | qb << 8)
+// with pa, qb the first nonzero slices over the tile's stored blocks.
 
-// Work items are enumerated in L2-friendly order: supertiles of IT row-block pairs
-// x JT block columns (IT * JT ~ one wave of CTAs), the column index fastest inside a
-// supertile. CTAs of one wave then share IT rows of A and JT columns of B while they
-// all walk k upwards, so operand slices are fetched from HBM about once per wave
-// instead of once per CTA.
+// Tiles are enumerated in L2-friendly order: supertiles of IT x JT tiles (about one
+// wave of CTAs), the column index fastest inside a supertile, so that the CTAs of a
+// wave share IT pair tiles of A and JT of B while they all walk k upwards.
 struct Raster {
-    int np, nb, it, jt, nsj;
+    int np, it, jt, nsj;
     __host__ __device__ int64_t size() const {
         return (int64_t)((np + it - 1) / it) * it * (int64_t)nsj * jt;
     }
-    __device__ bool unswizzle(int64_t b, int* I, int* j) const {
+    __device__ bool unswizzle(int64_t b, int* I, int* J) const {
         const int64_t per = (int64_t)it * jt;
         const int64_t st = b / per;
         const int r = (int)(b % per);
-        const int sI = (int)(st / nsj), sj = (int)(st % nsj);
+        const int sI = (int)(st / nsj), sJ = (int)(st % nsj);
         *I = sI * it + r / jt;
-        *j = sj * jt + r % jt;
-        return *I < np && *j < nb;
+        *J = sJ * jt + r % jt;
+        return *I < np && *J < np;
     }
 };
 
-__global__ void k_pair_count(ChargeData ch, Raster rs, const int32_t* __restrict__ out_flag,
-                             const int32_t* __restrict__ mapX, int sym,
-                             const double* __restrict__ d_tau, int32_t* __restrict__ cnt,
-                             int32_t* __restrict__ wflag) {
-    const int nb = ch.nb;
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= rs.size()) return;
-    int I, j;
-    const bool valid = rs.unswizzle(b, &I, &j);
-    const int i0 = 2 * I, i1 = 2 * I + 1;
-    int c = 0, work = 0;
-    if (valid && (!sym || i0 <= j)) {
-        const double tau = *d_tau;
-        for (int k = 0; k < nb; ++k) {
-            int32_t sa, sb;
-            bool kt = mx_keep(ch, i0, k, j, tau, &sa, &sb);
-            bool kb = (i1 < nb) && mx_keep(ch, i1, k, j, tau, &sa, &sb);
-            if (kt || kb) ++c;
-        }
-        const int64_t b0 = (int64_t)i0 * nb + j, b1 = (int64_t)i1 * nb + j;
-        work = out_flag[b0] || (mapX && mapX[b0] >= 0);
-        if (i1 < nb) work = work || out_flag[b1] || (mapX && mapX[b1] >= 0);
-    }
-    cnt[b] = work ? c : 0;
-    wflag[b] = work;
+struct TilePlan {
+    const double* nA;
+    const double* nB;
+    const int32_t* mapA;
+    const int32_t* mapB;      // B's block map (unused when sym: the B operand is X itself)
+    const int32_t* mapX;      // SP2 steps: blocks of X (the 2X - X^2 epilogue and the pattern)
+    const int64_t* pidxA;     // pair tiles of A: [(I, k)]
+    const int64_t* pidxB;     // pair tiles of the B operand: [(J, k)]
+    const int8_t* p0A;        // first nonzero slice per stored block (slot)
+    const int8_t* p0B;
+    int nb;
+    int sym;
+    int lmax;
+};
+
+__device__ __forceinline__ double nrm(const double* n, int nb, int r, int c) {
+    return (r < nb && c < nb) ? n[(int64_t)r * nb + c] : 0.0;
+}
+
+// slot of the B operand block (k, j): X's block (j, k) for a symmetric step
+__device__ __forceinline__ int32_t b_slot(const TilePlan& tp, int k, int j) {
+    if (j >= tp.nb) return -1;
+    return tp.sym ? tp.mapA[(int64_t)j * tp.nb + k] : tp.mapB[(int64_t)k * tp.nb + j];
 }
 
 __device__ __forceinline__ int n_level_pairs(int pa, int qb, int L) {
@@ -413,47 +415,106 @@ __device__ __forceinline__ int n_level_pairs(int pa, int qb, int L) {
     return n;
 }
 
-__global__ void k_pair_fill(ChargeData ch, Raster rs, const int32_t* __restrict__ out_flag,
-                            const int64_t* __restrict__ out_idx, int sym,
-                            const double* __restrict__ d_tau, const int32_t* __restrict__ wflag,
-                            const int64_t* __restrict__ widx, const int64_t* __restrict__ toff,
-                            int32_t* __restrict__ work_ij, int32_t* __restrict__ work_out,
-                            int64_t* __restrict__ work_off, int32_t* __restrict__ task,
-                            const int8_t* __restrict__ p0A, const int8_t* __restrict__ p0B,
-                            const int64_t* __restrict__ pair_idx,
-                            unsigned long long* __restrict__ counters) {
-    const int nb = ch.nb;
+// per tile: number of tasks, whether it has outputs, the output pattern, and the
+// candidate / kept triple counts of the full product (counters[0], counters[1])
+__global__ void k_tile_count(TilePlan tp, Raster rs, const double* __restrict__ d_tau,
+                             int32_t* __restrict__ cnt, int32_t* __restrict__ wflag,
+                             int32_t* __restrict__ out_flag,
+                             unsigned long long* __restrict__ counters) {
+    const int nb = tp.nb;
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long cand = 0, kept = 0;
+    int c = 0, work = 0;
+    int I = 0, J = 0;
+    if (b < rs.size() && rs.unswizzle(b, &I, &J) && (!tp.sym || I <= J)) {
+        const double tau = *d_tau;
+        const int i0 = 2 * I, j0 = 2 * J;
+        int f = 0;   // bit 2h + c: block (i0 + h, j0 + c) has a formed product
+        unsigned long long cd = 0, kp = 0;
+        for (int k = 0; k < nb; ++k) {
+            const double a0 = nrm(tp.nA, nb, i0, k), a1 = nrm(tp.nA, nb, i0 + 1, k);
+            const double b0 = nrm(tp.nB, nb, k, j0), b1 = nrm(tp.nB, nb, k, j0 + 1);
+            const double p[4] = {a0 * b0, a0 * b1, a1 * b0, a1 * b1};
+            const double m = fmax(a0, a1) * fmax(b0, b1);
+            const bool trig = m > 0.0 && m >= tau;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cd += p[q] > 0.0;
+                kp += p[q] > 0.0 && p[q] >= tau;
+                if (trig && p[q] > 0.0) f |= 1 << q;
+            }
+            c += trig;
+        }
+        const bool mirror = tp.sym && I < J;
+        cand = mirror ? 2 * cd : cd;
+        kept = mirror ? 2 * kp : kp;
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + (q >> 1), j = j0 + (q & 1);
+            if (i >= nb || j >= nb) continue;
+            const bool o = ((f >> q) & 1) || (tp.mapX && tp.mapX[(int64_t)i * nb + j] >= 0);
+            out_flag[(int64_t)i * nb + j] = o;
+            if (mirror) out_flag[(int64_t)j * nb + i] = o;
+            work |= o;
+        }
+    }
+    if (b < rs.size()) {
+        cnt[b] = work ? c : 0;
+        wflag[b] = work;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        cand += __shfl_xor_sync(0xffffffffu, cand, o);
+        kept += __shfl_xor_sync(0xffffffffu, kept, o);
+    }
+    if ((threadIdx.x & 31) == 0 && cand) {
+        atomicAdd(counters, cand);
+        atomicAdd(counters + 1, kept);
+    }
+}
+
+// per tile with outputs: work item, output slots, tasks; counters[0] formed products,
+// counters[1] (p, q) slice pairs issued over all passes
+__global__ void k_tile_fill(TilePlan tp, Raster rs, const int32_t* __restrict__ out_flag,
+                            const int64_t* __restrict__ out_idx, const double* __restrict__ d_tau,
+                            const int32_t* __restrict__ wflag, const int64_t* __restrict__ widx,
+                            const int64_t* __restrict__ toff, int32_t* __restrict__ work_ij,
+                            int32_t* __restrict__ work_out, int64_t* __restrict__ work_off,
+                            int32_t* __restrict__ task, unsigned long long* __restrict__ counters) {
+    const int nb = tp.nb;
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long formed = 0, pairs = 0;
-    int I = 0, j = 0;
-    if (b < rs.size() && wflag[b] && rs.unswizzle(b, &I, &j)) {
-        const int i0 = 2 * I, i1 = 2 * I + 1;
+    int I = 0, J = 0;
+    if (b < rs.size() && wflag[b] && rs.unswizzle(b, &I, &J)) {
+        const int i0 = 2 * I, j0 = 2 * J;
         const int64_t w = widx[b];
-        work_ij[w] = (int32_t)((int64_t)I * nb + j);
-        const int64_t b0 = (int64_t)i0 * nb + j, b1 = (int64_t)i1 * nb + j;
-        int32_t* wo = work_out + 4 * w;   // top, bottom, top mirror, bottom mirror
-        wo[0] = out_flag[b0] ? (int32_t)out_idx[b0] : -1;
-        wo[1] = (i1 < nb && out_flag[b1]) ? (int32_t)out_idx[b1] : -1;
-        const bool mir = sym && j > i1;
-        wo[2] = (mir && out_flag[(int64_t)j * nb + i0]) ? (int32_t)out_idx[(int64_t)j * nb + i0] : -1;
-        wo[3] = (mir && out_flag[(int64_t)j * nb + i1]) ? (int32_t)out_idx[(int64_t)j * nb + i1] : -1;
+        work_ij[w] = I * rs.np + J;
+        const bool mirror = tp.sym && I < J;
+        int32_t* wo = work_out + 8 * w;   // [2h + c] direct, [4 + 2h + c] transposed copy
+        for (int q = 0; q < 4; ++q) {
+            const int i = i0 + (q >> 1), j = j0 + (q & 1);
+            const bool in = i < nb && j < nb;
+            wo[q] = (in && out_flag[(int64_t)i * nb + j]) ? (int32_t)out_idx[(int64_t)i * nb + j] : -1;
+            wo[4 + q] = (in && mirror && out_flag[(int64_t)j * nb + i])
+                            ? (int32_t)out_idx[(int64_t)j * nb + i]
+                            : -1;
+        }
         int64_t t = toff[b];
         work_off[w] = t;
         const double tau = *d_tau;
         for (int k = 0; k < nb; ++k) {
-            int32_t sa0, sb0, sa1 = -1, sb1 = -1;
-            bool kt = mx_keep(ch, i0, k, j, tau, &sa0, &sb0);
-            bool kb = (i1 < nb) && mx_keep(ch, i1, k, j, tau, &sa1, &sb1);
-            if (!(kt || kb)) continue;
-            const int32_t s0 = kt ? sa0 : -1, s1 = kb ? sa1 : -1, sb = kt ? sb0 : sb1;
-            const bool whole = (kt || sa0 < 0) && (kb || i1 >= nb || sa1 < 0);
-            task[4 * t + 0] = s0;
-            task[4 * t + 1] = s1;
-            task[4 * t + 2] = sb;
-            task[4 * t + 3] = (int32_t)(2 * pair_idx[(int64_t)I * nb + k] + (whole ? 1 : 0));
-            formed += (kt ? 1 : 0) + (kb ? 1 : 0);
-            const int pa = min(s0 >= 0 ? (int)p0A[s0] : MX_S + 1, s1 >= 0 ? (int)p0A[s1] : MX_S + 1);
-            pairs += n_level_pairs(pa, p0B[sb], ch.lmax);
+            const double a0 = nrm(tp.nA, nb, i0, k), a1 = nrm(tp.nA, nb, i0 + 1, k);
+            const double b0 = nrm(tp.nB, nb, k, j0), b1 = nrm(tp.nB, nb, k, j0 + 1);
+            const double m = fmax(a0, a1) * fmax(b0, b1);
+            if (!(m > 0.0 && m >= tau)) continue;
+            const int32_t s0 = tp.mapA[(int64_t)i0 * nb + k];
+            const int32_t s1 = i0 + 1 < nb ? tp.mapA[(int64_t)(i0 + 1) * nb + k] : -1;
+            const int32_t t0 = b_slot(tp, k, j0), t1 = b_slot(tp, k, j0 + 1);
+            const int pa = min(s0 >= 0 ? (int)tp.p0A[s0] : MX_S + 1, s1 >= 0 ? (int)tp.p0A[s1] : MX_S + 1);
+            const int qb = min(t0 >= 0 ? (int)tp.p0B[t0] : MX_S + 1, t1 >= 0 ? (int)tp.p0B[t1] : MX_S + 1);
+            task[3 * t + 0] = (int32_t)tp.pidxA[(int64_t)I * nb + k];
+            task[3 * t + 1] = (int32_t)tp.pidxB[(int64_t)J * nb + k];
+            task[3 * t + 2] = pa | (qb << 8);
+            formed += (a0 * b0 > 0.0) + (a0 * b1 > 0.0) + (a1 * b0 > 0.0) + (a1 * b1 > 0.0);
+            pairs += n_level_pairs(pa, qb, tp.lmax);
             ++t;
         }
     }
@@ -473,69 +534,73 @@ __global__ void k_last_off(int64_t* work_off, int64_t n_work, const int64_t* tof
 
 // ------------------------------------------------------ the tcgen05 kernel
 
-constexpr int GM_STAGES = 4;
-constexpr int STAGE_A = MX_S * 2 * CHUNK;   // S slices x (two 64-row chunks)
-constexpr int STAGE_B = MX_S * CHUNK;
-constexpr int STAGE_BYTES = STAGE_A + STAGE_B;
-constexpr int GM_THREADS = 18 * 32;         // warp 0 copies, warp 1 issues MMAs, 16 fold/epilogue
-constexpr int GM_SMEM = GM_STAGES * STAGE_BYTES + 1024;
-constexpr int MAX_LEVELS = 8;               // 8 x 64 = all 512 TMEM columns
+constexpr int GM_THREADS = 18 * 32;   // warp 0 copies, warp 1 issues MMAs, 16 fold/epilogue
+constexpr int MAX_LEVELS = 4;         // 4 levels x 128 columns = all 512 TMEM columns
 constexpr long long WAIT_LIMIT = 1ll << 22;
+constexpr int SMEM_BUDGET = 220 * 1024;
 
-struct MixedArgs {
+// Stage layout of a pass over levels LO..HI: the slices 1..SMAX of the A and of the B
+// pair tile for one K chunk, each [slice][half][2 KB] (the M = 128 and N = 128
+// operand orders). SMAX = HI - 1 (at most 9) is the highest slice any pair uses.
+template <int LO, int HI>
+struct PassShape {
+    static constexpr int SMAX = HI - 1 < MX_S ? HI - 1 : MX_S;
+    static constexpr int HALF = SMAX * 2 * CHUNK;           // A (or B) part of a stage
+    static constexpr int STAGE = 2 * HALF;
+    static constexpr int NST = SMEM_BUDGET / STAGE < 6 ? SMEM_BUDGET / STAGE : 6;
+    static constexpr int SMEM = NST * STAGE + 1024;
+};
+
+struct TileArgs {
     const uint8_t* pairA;        // pair tiles of A
-    const uint8_t* slB;          // block tiles of the B operand
-    const int8_t* p0A;
-    const int8_t* p0B;
-    const int32_t* expA;
-    const int32_t* expB;
-    const uint8_t* zero_chunk;   // CHUNK bytes of zeros
-    const int32_t* task;         // [4 * n_tasks]
-    const int32_t* work_ij;
-    const int32_t* work_out;     // [4 * n_work]
+    const uint8_t* pairB;        // pair tiles of the B operand
+    const int32_t* expA;         // row exponents of A
+    const int32_t* expB;         // column exponents of B
+    const int32_t* task;         // [3 * n_tasks]
+    const int32_t* work_ij;      // I * np + J
+    const int32_t* work_out;     // [8 * n_work]
     const int64_t* work_off;
-    int nb;
-    int lv_lo, lv_hi;            // levels p + q formed by this pass (lv_hi - lv_lo < 8)
+    int nb, np;
     int window;                  // leaf products per exact-accumulation window
     int mode;                    // 0: C; 1: Xn = C; 2: Xn = 2X - C
-    int raw_out;                 // 1: write this pass's raw product into the output slots
+    int raw_out;                 // 1: write this pass's raw product (plus add_prev) and stop
     int add_prev;                // 1: add the raw product already in the output slots
     const int32_t* mapX;
     const double* tilesX;
     double* tilesC;
     double* normC;
-    double* part_fro2;           // [2 * n_work]
+    double* part_fro2;           // [4 * n_work]
     double* part_trace;
     double* part_idem2;
     int* status;
 };
 
-__device__ __forceinline__ int tile_p0(const int8_t* p0, int32_t s) { return s >= 0 ? p0[s] : MX_S + 1; }
-
-// LO..HI: the levels p + q this pass forms (compile time, so that the MMA issue loop
-// unrolls into constant descriptor offsets)
+// One pass over the levels LO..HI (at most 4) of one tile: f32 level accumulators of
+// 128 x 128 in TMEM, folded every `window` leaf products into one int64 per entry,
+// V = sum_lv g_lv 2^(7 (HI - lv)), |g_lv| < 2^24 per window.
 template <int LO, int HI>
-__global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
+__global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
+    using PS = PassShape<LO, HI>;
     static_assert(HI - LO < MAX_LEVELS && LO >= 2 && HI <= 2 * MX_S, "levels must fit in TMEM");
+    constexpr int SMAX = PS::SMAX, HALF = PS::HALF, STAGE = PS::STAGE, NST = PS::NST;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* stages = smem;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + GM_STAGES * STAGE_BYTES);
-    // bars: full[4], empty[4], acc_full, acc_empty, drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 11);
-    volatile int* s_err = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    int* hdr = reinterpret_cast<int*>(smem + GM_STAGES * STAGE_BYTES + 96);        // [4] pa | qb<<8
-    double* red = reinterpret_cast<double*>(smem + GM_STAGES * STAGE_BYTES + 128);   // [16][3]
+    uint8_t* ctl = smem + NST * STAGE;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ctl);   // full[NST], empty[NST], accf, acce, drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ctl + 128);
+    volatile int* s_err = reinterpret_cast<volatile int*>(ctl + 132);
+    int* hdr = reinterpret_cast<int*>(ctl + 160);              // [NST] pa | qb << 8
+    double* red = reinterpret_cast<double*>(ctl + 256);        // [16][3]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w = blockIdx.x;
     const int64_t t0 = a.work_off[w], t1 = a.work_off[w + 1];
     const int ntask = (int)(t1 - t0);
     const int nwin = (ntask + a.window - 1) / a.window;
-    constexpr int lo = LO, hi = HI;
-    const uint32_t b_full = tc::smem_u32(bars), b_empty = tc::smem_u32(bars + 4);
-    const uint32_t b_accf = tc::smem_u32(bars + 8), b_acce = tc::smem_u32(bars + 9);
-    const uint32_t b_drain = tc::smem_u32(bars + 10);
+    const uint32_t b_full = tc::smem_u32(bars), b_empty = tc::smem_u32(bars + NST);
+    const uint32_t b_accf = tc::smem_u32(bars + 2 * NST), b_acce = tc::smem_u32(bars + 2 * NST + 1);
+    const uint32_t b_drain = tc::smem_u32(bars + 2 * NST + 2);
     if (tid == 0) {
-        for (int i = 0; i < GM_STAGES; ++i) {
+        for (int i = 0; i < NST; ++i) {
             tc::mbar_init(b_full + 8 * i, 1);
             tc::mbar_init(b_empty + 8 * i, 1);
         }
@@ -553,69 +618,51 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
 
     if (warp == 0) {
         // -------------------------------------------- producer (whole warp)
-        // lanes load the metadata of 32 tasks at a time; each stage's copies are
-        // issued by one lane each; lane 0 handles the barriers and the stage header
+        // lanes load the metadata of 32 tasks at a time; per stage lane 0 copies the
+        // A slices pa..pmax and lane 1 the B slices qb..qmax, each one contiguous run
         int it = 0;
         bool ok = true;
         for (int64_t base = t0; base < t1 && ok; base += 32) {
             const int64_t tl = base + lane;
-            int32_t s0 = -1, s1 = -1, sb = 0, pw = 0;
-            int pa = MX_S + 1, qb = MX_S + 1;
+            int32_t pA = 0, pB = 0, pq = (MX_S + 1) | ((MX_S + 1) << 8);
             if (tl < t1) {
-                s0 = a.task[4 * tl];
-                s1 = a.task[4 * tl + 1];
-                sb = a.task[4 * tl + 2];
-                pw = a.task[4 * tl + 3];
-                pa = min(tile_p0(a.p0A, s0), tile_p0(a.p0A, s1));
-                qb = tile_p0(a.p0B, sb);
+                pA = a.task[3 * tl];
+                pB = a.task[3 * tl + 1];
+                pq = a.task[3 * tl + 2];
             }
             const int cnt = (int)min((int64_t)32, t1 - base);
             for (int j = 0; j < cnt && ok; ++j) {
-                const int32_t js0 = __shfl_sync(0xffffffffu, s0, j);
-                const int32_t js1 = __shfl_sync(0xffffffffu, s1, j);
-                const int32_t jsb = __shfl_sync(0xffffffffu, sb, j);
-                const int32_t jpw = __shfl_sync(0xffffffffu, pw, j);
-                const uint8_t* pt = a.pairA + (int64_t)(jpw >> 1) * PAIR_BYTES;
-                const uint8_t* bt = a.slB + (int64_t)jsb * TILE_BYTES;
-                const int jpa = __shfl_sync(0xffffffffu, pa, j);
-                const int jqb = __shfl_sync(0xffffffffu, qb, j);
-                const int pmax = min(MX_S, hi - jqb), qmax = min(MX_S, hi - jpa);
-                const int np = pmax >= jpa ? pmax - jpa + 1 : 0;
-                const int nq = qmax >= jqb ? qmax - jqb + 1 : 0;
-                for (int c = 0; c < 4; ++c, ++it) {
-                    const int st = it % GM_STAGES;
+                const int32_t jA = __shfl_sync(0xffffffffu, pA, j);
+                const int32_t jB = __shfl_sync(0xffffffffu, pB, j);
+                const int jpq = __shfl_sync(0xffffffffu, pq, j);
+                const int pa = jpq & 0xff, qb = jpq >> 8;
+                const int pmax = min(SMAX, HI - qb), qmax = min(SMAX, HI - pa);
+                const int np = pmax >= pa ? pmax - pa + 1 : 0;
+                const int nq = qmax >= qb ? qmax - qb + 1 : 0;
+                const uint8_t* ga = a.pairA + (int64_t)jA * PAIR_BYTES + (pa - 1) * 2 * CHUNK;
+                const uint8_t* gb = a.pairB + (int64_t)jB * PAIR_BYTES + (qb - 1) * 2 * CHUNK;
+                for (int c = 0; c < KCH; ++c, ++it) {
+                    const int st = it % NST;
                     bool got = true;
                     if (lane == 0) {
-                        got = tc::mbar_wait(b_empty + 8 * st, ((it / GM_STAGES) & 1) ^ 1, WAIT_LIMIT);
+                        got = tc::mbar_wait(b_empty + 8 * st, ((it / NST) & 1) ^ 1, WAIT_LIMIT);
                         if (got) {
-                            hdr[st] = jpa | (jqb << 8);
-                            tc::mbar_arrive_expect_tx(b_full + 8 * st, (uint32_t)(2 * np + nq) * CHUNK);
+                            hdr[st] = jpq;
+                            tc::mbar_arrive_expect_tx(b_full + 8 * st, (uint32_t)(np + nq) * 2 * CHUNK);
                         } else {
                             atomicExch((int*)s_err, 1);
                         }
                     }
                     ok = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
                     if (!ok) break;
-                    const uint32_t sA = tc::smem_u32(stages + st * STAGE_BYTES);
-                    const uint32_t sB = sA + STAGE_A;
-                    // A: slices jpa..pmax of both halves, one run of the pair tile; when a
-                    // stored half is not kept, per-slice copies with zeros for that half
-                    if (jpw & 1) {
-                        if (lane == 0 && np > 0)
-                            tc::bulk_g2s(sA + (jpa - 1) * 2 * CHUNK,
-                                         pt + c * PAIR_CSTRIDE + (jpa - 1) * 2 * CHUNK,
-                                         (uint32_t)np * 2 * CHUNK, b_full + 8 * st);
-                    } else if (lane < 2 * np) {
-                        const int p = jpa + (lane >> 1), half = lane & 1;
-                        const int32_t sl = half ? js1 : js0;
-                        const uint8_t* g = sl >= 0 ? pt + c * PAIR_CSTRIDE + (p - 1) * 2 * CHUNK + half * CHUNK
-                                                   : a.zero_chunk;
-                        tc::bulk_g2s(sA + (p - 1) * 2 * CHUNK + half * CHUNK, g, CHUNK, b_full + 8 * st);
-                    }
-                    // B: slices jqb..qmax, one run of the block tile
-                    if (lane == 31 && nq > 0)
-                        tc::bulk_g2s(sB + (jqb - 1) * CHUNK, bt + c * TILE_CSTRIDE + (jqb - 1) * CHUNK,
-                                     (uint32_t)nq * CHUNK, b_full + 8 * st);
+                    const uint32_t sA = tc::smem_u32(stages + st * STAGE);
+                    const uint32_t sB = sA + HALF;
+                    if (lane == 0 && np > 0)
+                        tc::bulk_g2s(sA + (pa - 1) * 2 * CHUNK, ga + c * PAIR_CSTRIDE,
+                                     (uint32_t)np * 2 * CHUNK, b_full + 8 * st);
+                    if (lane == 1 && nq > 0)
+                        tc::bulk_g2s(sB + (qb - 1) * 2 * CHUNK, gb + c * PAIR_CSTRIDE,
+                                     (uint32_t)nq * 2 * CHUNK, b_full + 8 * st);
                 }
             }
         }
@@ -623,9 +670,10 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
         // ------------------------------------- MMA issuer (converged warp)
         // The whole warp runs the loop so that its control stays warp-uniform; one
         // elected lane issues the MMAs and the commits.
-        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 64);
+        constexpr uint32_t idesc = tc::idesc_bf16_f32(128, 128);
         const uint64_t dA0 = tc::desc_kmajor(tc::smem_u32(stages), 128, 256);
-        const uint64_t dB0 = tc::desc_kmajor(tc::smem_u32(stages + STAGE_A), 128, 256);
+        const uint64_t dB0 = tc::desc_kmajor(tc::smem_u32(stages + HALF), 128, 256);
+        constexpr uint64_t SL = (2 * CHUNK) >> 4;   // descriptor step of one slice
         const uint32_t e = tc::elect_one();
         int it = 0;
         int64_t t = t0;
@@ -639,10 +687,10 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
             tc::fence_after();
             const int64_t tend = min(t1, t + a.window);
             for (; t < tend && ok; ++t) {
-                for (int c = 0; c < 4; ++c, ++it) {
-                    const int st = it % GM_STAGES;
+                for (int c = 0; c < KCH; ++c, ++it) {
+                    const int st = it % NST;
                     ok = __all_sync(0xffffffffu,
-                                    tc::mbar_wait(b_full + 8 * st, (it / GM_STAGES) & 1, WAIT_LIMIT));
+                                    tc::mbar_wait(b_full + 8 * st, (it / NST) & 1, WAIT_LIMIT));
                     if (!ok) {
                         if (e) atomicExch((int*)s_err, 3);
                         break;
@@ -650,31 +698,32 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
                     tc::fence_after();
                     const int h = hdr[st];
                     const int pa = h & 0xff, qb = h >> 8;
-                    const uint64_t dAs = dA0 + (uint64_t)((st * STAGE_BYTES) >> 4);
-                    const uint64_t dBs = dB0 + (uint64_t)((st * STAGE_BYTES) >> 4);
-                    if constexpr (LO == 2) {
+                    const uint64_t dAs = dA0 + (uint64_t)((st * STAGE) >> 4);
+                    const uint64_t dBs = dB0 + (uint64_t)((st * STAGE) >> 4);
+                    if constexpr (HI - LO >= 2) {
                         // many (p, q) per level: loops whose trip counts follow pa, qb
-                        for (int p = pa; p <= MX_S && p + qb <= HI; ++p) {
-                            const uint64_t da = dAs + (uint64_t)(((p - 1) * 2 * CHUNK) >> 4);
-                            const int q1 = min(MX_S, HI - p);
-                            uint64_t db = dBs + (uint64_t)(((qb - 1) * CHUNK) >> 4);
-                            uint32_t dcol = tmem + (uint32_t)(p + qb - LO) * 64;
-                            for (int q = qb; q <= q1; ++q) {
+                        for (int p = pa; p <= SMAX && p + qb <= HI; ++p) {
+                            const int q0 = max(qb, LO - p), q1 = min(SMAX, HI - p);
+                            if (q0 > q1) continue;
+                            const uint64_t da = dAs + (uint64_t)(p - 1) * SL;
+                            uint64_t db = dBs + (uint64_t)(q0 - 1) * SL;
+                            uint32_t dcol = tmem + (uint32_t)(p + q0 - LO) * 128;
+                            for (int q = q0; q <= q1; ++q) {
                                 if (e) tc::mma_bf16(dcol, da, db, idesc, 1u);
-                                db += (uint64_t)(CHUNK >> 4);
-                                dcol += 64;
+                                db += SL;
+                                dcol += 128;
                             }
                         }
                     } else {
                         // one or two q per p: unrolled over the pass's (p, q)
 #pragma unroll
-                        for (int p = 1; p <= MX_S; ++p) {
+                        for (int p = 1; p <= SMAX; ++p) {
 #pragma unroll
-                            for (int q = 1; q <= MX_S; ++q) {
+                            for (int q = 1; q <= SMAX; ++q) {
                                 if (p + q >= LO && p + q <= HI && p >= pa && q >= qb && e)
-                                    tc::mma_bf16(tmem + (uint32_t)(p + q - LO) * 64,
-                                                 dAs + (uint64_t)(((p - 1) * 2 * CHUNK) >> 4),
-                                                 dBs + (uint64_t)(((q - 1) * CHUNK) >> 4), idesc, 1u);
+                                    tc::mma_bf16(tmem + (uint32_t)(p + q - LO) * 128,
+                                                 dAs + (uint64_t)(p - 1) * SL,
+                                                 dBs + (uint64_t)(q - 1) * SL, idesc, 1u);
                             }
                         }
                     }
@@ -695,12 +744,15 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
         // ------------------------------------------ fold + epilogue (16 warps)
         const int ew = warp - 2;
         const int quarter = warp & 3;           // TMEM lanes 32*quarter .. +31
-        const int cb = ew >> 2;                 // columns 16*cb .. +15
-        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cb * 16);
-        long long H[16], Lo[16];
+        const int cb = ew >> 2;                 // columns 32*cb .. +31
+        const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cb * 32);
+        long long acc[32];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) H[j] = Lo[j] = 0;
-        for (int lv = lo; lv <= hi; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - lo) * 64);
+        for (int j = 0; j < 32; ++j) acc[j] = 0;
+        for (int lv = LO; lv <= HI; ++lv) {
+            tc::tmem_st16_zero(trow + (uint32_t)(lv - LO) * 128);
+            tc::tmem_st16_zero(trow + (uint32_t)(lv - LO) * 128 + 16);
+        }
         tc::tmem_st_wait();
         tc::fence_before();
         __syncwarp();
@@ -714,20 +766,23 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
             }
             tc::fence_after();
             // each exact level sum g (|g| < 2^24, converted in int32) enters V with
-            // weight 2^sh, sh = 7 (hi - lv)
-            for (int lv = lo; lv <= hi; ++lv) {
-                uint32_t v[16];
-                tc::tmem_ld16(trow + (uint32_t)(lv - lo) * 64, v);
-                tc::tmem_ld_wait();
-                const int sh = MX_W * (hi - lv);     // weight of this level in V
+            // weight 2^(7 (HI - lv)) <= 2^21
+            for (int lv = LO; lv <= HI; ++lv) {
+                const int sh = MX_W * (HI - lv);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const long long g = (long long)__float2int_rn(__uint_as_float(v[j]));
-                    if (sh < 28) Lo[j] += g << sh;
-                    else H[j] += g << (sh - 28);
+                for (int hf = 0; hf < 2; ++hf) {
+                    uint32_t v[16];
+                    tc::tmem_ld16(trow + (uint32_t)(lv - LO) * 128 + hf * 16, v);
+                    tc::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        acc[hf * 16 + j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
                 }
             }
-            for (int lv = lo; lv <= hi; ++lv) tc::tmem_st16_zero(trow + (uint32_t)(lv - lo) * 64);
+            for (int lv = LO; lv <= HI; ++lv) {
+                tc::tmem_st16_zero(trow + (uint32_t)(lv - LO) * 128);
+                tc::tmem_st16_zero(trow + (uint32_t)(lv - LO) * 128 + 16);
+            }
             tc::tmem_st_wait();
             tc::fence_before();
             __syncwarp();
@@ -736,38 +791,38 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
         // ---- values, SP2 combination, writes, partial sums
         const int nb = a.nb;
         const int32_t ij = a.work_ij[w];
-        const int I = ij / nb, jb = ij % nb;
+        const int I = ij / a.np, J = ij % a.np;
         const int rl = quarter * 32 + lane;      // 0..127
-        const int half = rl >> 6, rr = rl & 63;
-        const int bi = 2 * I + half;
-        const int32_t os = a.work_out[4 * w + half];
-        const int32_t ost = a.work_out[4 * w + 2 + half];
+        const int h = rl >> 6, rr = rl & 63;
+        const int cc = cb >> 1, sc0 = (cb & 1) * 32;
+        const int bi = 2 * I + h, bj = 2 * J + cc;
         double fro2 = 0.0, tr = 0.0, idem2 = 0.0;
-        if (bi < nb) {
+        if (bi < nb && bj < nb) {
+            const int32_t os = a.work_out[8 * w + 2 * h + cc];
+            const int32_t ost = a.work_out[8 * w + 4 + 2 * h + cc];
             const int er = a.expA[bi * MX_BS + rr];
             const double* X = nullptr;
             if (a.mode != 0 && a.mapX) {
-                const int32_t xs = a.mapX[(int64_t)bi * nb + jb];
+                const int32_t xs = a.mapX[(int64_t)bi * nb + bj];
                 if (xs >= 0) X = a.tilesX + (int64_t)xs * MX_BS * MX_BS;
             }
             double* Co = os >= 0 ? a.tilesC + (int64_t)os * MX_BS * MX_BS : nullptr;
             double* Ct = ost >= 0 ? a.tilesC + (int64_t)ost * MX_BS * MX_BS : nullptr;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int sc = cb * 16 + j;
-                const int fs = a.expB[jb * MX_BS + sc];
-                const double v = fma((double)H[j], 268435456.0, (double)Lo[j]);   // H 2^28 + Lo
-                double cv = ldexp(v, er + fs - MX_W * hi);
+            for (int j = 0; j < 32; ++j) {
+                const int sc = sc0 + j;
+                const int fs = a.expB[bj * MX_BS + sc];
+                double cv = ldexp((double)acc[j], er + fs - MX_W * HI);
+                if (a.add_prev && Co) cv += Co[rr * MX_BS + sc];
                 if (a.raw_out) {
                     if (Co) Co[rr * MX_BS + sc] = cv;
                     continue;
                 }
-                if (a.add_prev && Co) cv += Co[rr * MX_BS + sc];
                 const double x = X ? X[rr * MX_BS + sc] : 0.0;
                 const double out = a.mode == 2 ? 2.0 * x - cv : cv;
                 if (a.mode != 0) idem2 = fma(cv - x, cv - x, idem2);
                 fro2 = fma(out, out, fro2);
-                if (bi == jb && rr == sc) tr += out;
+                if (bi == bj && rr == sc) tr += out;
                 if (Co) Co[rr * MX_BS + sc] = out;
                 if (Ct) Ct[sc * MX_BS + rr] = out;
             }
@@ -785,28 +840,29 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
     }
     tc::fence_before();
     __syncthreads();
-    if (tid < 2 && !a.raw_out) {
-        // half h: epilogue warps whose quarter is 2h or 2h+1, in warp order
-        const int h = tid;
+    if (tid < 4 && !a.raw_out) {
+        // block q = 2h + c of the tile: the four epilogue warps whose lane quarter has
+        // half h and whose column group has block column c, in warp order
+        const int q = tid, hq = q >> 1, cq = q & 1;
         double f = 0.0, tr = 0.0, id = 0.0;
         for (int ew = 0; ew < 16; ++ew) {
             const int quarter = (ew + 2) & 3;
-            if ((quarter >> 1) != h) continue;
+            if ((quarter >> 1) != hq || ((ew >> 2) >> 1) != cq) continue;
             f += red[ew * 3 + 0];
             tr += red[ew * 3 + 1];
             id += red[ew * 3 + 2];
         }
-        const int32_t ost = a.work_out[4 * w + 2 + h];
+        const int32_t os = a.work_out[8 * w + q], ost = a.work_out[8 * w + 4 + q];
         const double mult = ost >= 0 ? 2.0 : 1.0;
-        a.part_fro2[2 * w + h] = mult * f;
-        a.part_trace[2 * w + h] = tr;
-        a.part_idem2[2 * w + h] = mult * id;
+        a.part_fro2[4 * w + q] = mult * f;
+        a.part_trace[4 * w + q] = tr;
+        a.part_idem2[4 * w + q] = mult * id;
         const int nb = a.nb;
         const int32_t ij = a.work_ij[w];
-        const int bi = 2 * (ij / nb) + h, jb = ij % nb;
-        const double nrm = sqrt(f);
-        if (a.work_out[4 * w + h] >= 0) a.normC[(int64_t)bi * nb + jb] = nrm;
-        if (ost >= 0) a.normC[(int64_t)jb * nb + bi] = nrm;
+        const int bi = 2 * (ij / a.np) + hq, bj = 2 * (ij % a.np) + cq;
+        const double nrmv = sqrt(f);
+        if (os >= 0) a.normC[(int64_t)bi * nb + bj] = nrmv;
+        if (ost >= 0) a.normC[(int64_t)bj * nb + bi] = nrmv;
     }
     if (tid == 0 && *s_err) atomicExch(a.status, *s_err);
     tc::fence_after();
@@ -815,40 +871,44 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_mixed(MixedArgs a) {
 
 // ------------------------------------------------------------- host side
 
-constexpr int MX_LMAX_MAIN = 2 + MAX_LEVELS - 1;   // levels 2..9 share TMEM in the main pass
+using GemmTileFn = void (*)(TileArgs);
 
-using GemmMixedFn = void (*)(MixedArgs);
+struct PassKernel {
+    GemmTileFn fn;
+    int smem;
+};
 
-// the instance for levels lo..hi: the main pass (lo = 2, hi = 4..9) or the pass over
-// the levels above it (lo = 10, hi = 10..MIXED_LMAX)
-static GemmMixedFn gemm_mixed_kernel(int lo, int hi) {
-    if (lo == 2) {
+// the instance for levels lo..hi: lo = 2 (hi = 4, 5), lo = 6 (hi = 6..9), lo = 10
+// (hi = 10, 11)
+static PassKernel pass_kernel(int lo, int hi) {
+#define SPAMM_PASS(L, H) PassKernel{k_gemm_tile<L, H>, PassShape<L, H>::SMEM}
+    if (lo == 2) return hi <= 4 ? SPAMM_PASS(2, 4) : SPAMM_PASS(2, 5);
+    if (lo == 6) {
         switch (hi) {
-            case 4: return k_gemm_mixed<2, 4>;
-            case 5: return k_gemm_mixed<2, 5>;
-            case 6: return k_gemm_mixed<2, 6>;
-            case 7: return k_gemm_mixed<2, 7>;
-            case 8: return k_gemm_mixed<2, 8>;
-            default: return k_gemm_mixed<2, 9>;
+            case 6: return SPAMM_PASS(6, 6);
+            case 7: return SPAMM_PASS(6, 7);
+            case 8: return SPAMM_PASS(6, 8);
+            default: return SPAMM_PASS(6, 9);
         }
     }
-    return hi <= 10 ? k_gemm_mixed<10, 10> : k_gemm_mixed<10, 11>;
+    return hi <= 10 ? SPAMM_PASS(10, 10) : SPAMM_PASS(10, 11);
+#undef SPAMM_PASS
 }
-static_assert(MX_LMAX_MAIN == 9 && MIXED_LMAX == 11, "instances above cover levels 4..11");
+static_assert(MIXED_LMAX == 11, "the pass instances cover levels 2..11");
 
-static uint8_t* g_zero_chunk[64] = {nullptr};
 static bool g_attr_set[64] = {false};
 static std::mutex g_mixed_init;   // one-time per-device set-up, shared by host threads
 
-static int zero_chunk(spamm_ctx* ctx, const uint8_t** out) {
+static int set_pass_attributes(spamm_ctx* ctx) {
     std::lock_guard<std::mutex> lock(g_mixed_init);
-    if (!g_zero_chunk[ctx->device]) {
-        uint8_t* p = nullptr;
-        SP_CUDA(cudaMalloc(&p, CHUNK));
-        SP_CUDA(cudaMemset(p, 0, CHUNK));
-        g_zero_chunk[ctx->device] = p;
+    if (ctx->device < 0 || ctx->device >= 64) return SPAMM_EINVAL;
+    if (g_attr_set[ctx->device]) return SPAMM_OK;
+    const int ranges[8][2] = {{2, 4}, {2, 5}, {6, 6}, {6, 7}, {6, 8}, {6, 9}, {10, 10}, {10, 11}};
+    for (const auto& r : ranges) {
+        const PassKernel k = pass_kernel(r[0], r[1]);
+        SP_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem));
     }
-    *out = g_zero_chunk[ctx->device];
+    g_attr_set[ctx->device] = true;
     return SPAMM_OK;
 }
 
@@ -862,13 +922,16 @@ int mixed_prepare(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, int sy
     }
     SliceSet* sa = new SliceSet();
     SliceSet* sb = sym ? sa : new SliceSet();
-    // A needs pair tiles; the B operand block tiles (for symmetric X, of X itself)
-    SP_TRY(split_matrix(ctx, A, 0, sym ? 1 : 0, 1, sa));
-    if (!sym) SP_TRY(split_matrix(ctx, B, 1, 1, 0, sb));
+    // pair tiles over block rows of A; over block columns of B (transposed split). A
+    // symmetric X serves as its own B operand: the pair tile (J, k) of X holds the
+    // blocks (k, 2J), (k, 2J + 1) of X in the B operand's K-major order.
+    int st = split_matrix(ctx, A, 0, 0, 1, sa);
+    if (st == SPAMM_OK && !sym) st = split_matrix(ctx, B, 1, 0, 1, sb);
     mp->sa = sa;
     mp->sb = sb;
     mp->sym = sym;
-    return SPAMM_OK;
+    if (st != SPAMM_OK) mixed_release(ctx, mp);
+    return st;
 }
 
 void mixed_release(spamm_ctx* ctx, MixedPrep* mp) {
@@ -910,154 +973,149 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     DevScalars* sc = (DevScalars*)ctx->d_scalars;
     const int nb = A->nb;
     const int64_t nb2 = (int64_t)nb * nb;
+    const int np = (nb + 1) / 2;
     const SliceSet* sa = (const SliceSet*)mp.sa;
     const SliceSet* sbs = (const SliceSet*)mp.sb;
-    ChargeData ch = mixed_charge(A, B, nA, nB, mp, lmax);
-    // block-level flags (kept under the mixed rule) -> output slots
+    TilePlan tp;
+    tp.nA = nA;
+    tp.nB = nB;
+    tp.mapA = A->d_map;
+    tp.mapB = B->d_map;
+    tp.mapX = mode ? A->d_map : nullptr;
+    tp.pidxA = sa->pair_idx;
+    tp.pidxB = sbs->pair_idx;
+    tp.p0A = sa->p0;
+    tp.p0B = sbs->p0;
+    tp.nb = nb;
+    tp.sym = sym;
+    tp.lmax = lmax;
+    Raster rs;
+    rs.np = np;
+    rs.it = 8;
+    rs.jt = (ctx->num_sms + 7) / 8;
+    rs.nsj = (np + rs.jt - 1) / rs.jt;
+    const int64_t ntile = rs.size();
     int32_t *cnt = nullptr, *wf = nullptr, *of = nullptr;
     int64_t *toff = nullptr, *widx = nullptr, *oidx = nullptr;
-    SP_TRY(dalloc((void**)&cnt, sizeof(int32_t) * nb2, s));
-    SP_TRY(dalloc((void**)&wf, sizeof(int32_t) * nb2, s));
+    unsigned long long* d_tot = nullptr;
+    SP_TRY(dalloc((void**)&cnt, sizeof(int32_t) * ntile, s));
+    SP_TRY(dalloc((void**)&wf, sizeof(int32_t) * ntile, s));
     SP_TRY(dalloc((void**)&of, sizeof(int32_t) * nb2, s));
-    SP_TRY(dalloc((void**)&toff, sizeof(int64_t) * (nb2 + 1), s));
-    SP_TRY(dalloc((void**)&widx, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&toff, sizeof(int64_t) * (ntile + 1), s));
+    SP_TRY(dalloc((void**)&widx, sizeof(int64_t) * (ntile + 1), s));
     SP_TRY(dalloc((void**)&oidx, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&d_tot, 16, s));
+    SP_CUDA(cudaMemsetAsync(of, 0, sizeof(int32_t) * nb2, s));
     SP_CUDA(cudaMemsetAsync(&sc->n_cand, 0, 2 * sizeof(unsigned long long), s));
-    SP_TRY(plan_count_blocks(ctx, A, B, nA, nB, d_tau, mode ? A : nullptr, mode == 2, sym, &ch, cnt,
-                             wf, of));
+    const unsigned G = (unsigned)((ntile + 255) / 256);
+    ++ctx->launches;
+    k_tile_count<<<G, 256, 0, s>>>(tp, rs, d_tau, cnt, wf, of, &sc->n_cand);
+    SP_CHECK_LAUNCH();
     SP_TRY(scan_i32_to_i64(ctx, of, oidx, nb2, &sc->n_out));
-    SP_TRY(scan_i32_to_i64(ctx, cnt, toff, nb2, &sc->n_tasks));   // formed products (blocks)
-    unsigned long long h[4];
+    SP_TRY(scan_i32_to_i64(ctx, cnt, toff, ntile, d_tot));
+    SP_TRY(scan_i32_to_i64(ctx, wf, widx, ntile, d_tot + 1));
+    unsigned long long h[3], ht[2];
     SP_CUDA(cudaMemcpyAsync(h, &sc->n_cand, 16, cudaMemcpyDeviceToHost, s));
     SP_CUDA(cudaMemcpyAsync(h + 2, &sc->n_out, 8, cudaMemcpyDeviceToHost, s));
-    SP_CUDA(cudaMemcpyAsync(h + 3, &sc->n_tasks, 8, cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaMemcpyAsync(ht, d_tot, 16, cudaMemcpyDeviceToHost, s));
     SP_CUDA(cudaStreamSynchronize(s));
     *n_cand = (int64_t)h[0];
     *n_kept = (int64_t)h[1];
-    *n_formed = (int64_t)h[3];
+    const int64_t n_task = (int64_t)ht[0], n_work = (int64_t)ht[1];
     spamm_mat* C = nullptr;
     SP_TRY(mat_alloc(ctx, A->n, A->bs, (int64_t)h[2], &C));
     C->nslots = C->nnzb = (int64_t)h[2];
-    // map and coordinates of the output
     SP_TRY(plan_write_out_map(ctx, of, oidx, nb, C));
-    // pair work items
-    const int np = (nb + 1) / 2;
-    Raster rs;
-    rs.np = np;
-    rs.nb = nb;
-    rs.it = 8;
-    rs.jt = (ctx->num_sms + 7) / 8;
-    rs.nsj = (nb + rs.jt - 1) / rs.jt;
-    const int64_t npb = rs.size();
-    int32_t *pc = nullptr, *pwf = nullptr;
-    int64_t *ptoff = nullptr, *pwidx = nullptr;
-    unsigned long long* d_tot = nullptr;
-    SP_TRY(dalloc((void**)&pc, sizeof(int32_t) * npb, s));
-    SP_TRY(dalloc((void**)&pwf, sizeof(int32_t) * npb, s));
-    SP_TRY(dalloc((void**)&ptoff, sizeof(int64_t) * (npb + 1), s));
-    SP_TRY(dalloc((void**)&pwidx, sizeof(int64_t) * (npb + 1), s));
-    SP_TRY(dalloc((void**)&d_tot, 16, s));
-    const unsigned G = (unsigned)((npb + 255) / 256);
-    ++ctx->launches;
-    k_pair_count<<<G, 256, 0, s>>>(ch, rs, of, mode ? A->d_map : nullptr, sym, d_tau, pc, pwf);
-    SP_CHECK_LAUNCH();
-    SP_TRY(scan_i32_to_i64(ctx, pc, ptoff, npb, d_tot));
-    SP_TRY(scan_i32_to_i64(ctx, pwf, pwidx, npb, d_tot + 1));
-    unsigned long long hp[2];
-    SP_CUDA(cudaMemcpyAsync(hp, d_tot, 16, cudaMemcpyDeviceToHost, s));
-    SP_CUDA(cudaStreamSynchronize(s));
-    const int64_t n_pt = (int64_t)hp[0], n_work = (int64_t)hp[1];
-    *n_pairs_out = n_pt;
+    const int64_t nw = n_work > 0 ? n_work : 1;
     int32_t *work_ij = nullptr, *work_out = nullptr, *task = nullptr;
     int64_t* work_off = nullptr;
     double* parts = nullptr;
-    const int64_t nw = n_work > 0 ? n_work : 1;
     SP_TRY(dalloc((void**)&work_ij, sizeof(int32_t) * nw, s));
-    SP_TRY(dalloc((void**)&work_out, sizeof(int32_t) * 4 * nw, s));
+    SP_TRY(dalloc((void**)&work_out, sizeof(int32_t) * 8 * nw, s));
     SP_TRY(dalloc((void**)&work_off, sizeof(int64_t) * (nw + 1), s));
-    SP_TRY(dalloc((void**)&task, sizeof(int32_t) * 4 * (n_pt > 0 ? n_pt : 1), s));
-    SP_TRY(dalloc((void**)&parts, sizeof(double) * 6 * nw, s));
+    SP_TRY(dalloc((void**)&task, sizeof(int32_t) * 3 * (n_task > 0 ? n_task : 1), s));
+    SP_TRY(dalloc((void**)&parts, sizeof(double) * 12 * nw, s));
     SP_CUDA(cudaMemsetAsync(&sc->mx_formed, 0, 2 * sizeof(unsigned long long), s));
     ++ctx->launches;
-    k_pair_fill<<<G, 256, 0, s>>>(ch, rs, of, oidx, sym, d_tau, pwf, pwidx, ptoff, work_ij, work_out,
-                                  work_off, task, sa->p0, sbs->p0, sa->pair_idx, &sc->mx_formed);
+    k_tile_fill<<<G, 256, 0, s>>>(tp, rs, of, oidx, d_tau, wf, widx, toff, work_ij, work_out,
+                                  work_off, task, &sc->mx_formed);
     ++ctx->launches;
-    k_last_off<<<1, 1, 0, s>>>(work_off, n_work, ptoff, npb);
+    k_last_off<<<1, 1, 0, s>>>(work_off, n_work, toff, ntile);
     SP_CHECK_LAUNCH();
+    *n_formed = 0;
+    *n_pairs_out = 0;
     int st = SPAMM_OK;
     if (n_work > 0) {
-        MixedArgs ga;
-        memset(&ga, 0, sizeof ga);
-        ga.pairA = sa->pairs;
-        ga.slB = sbs->slices;
-        ga.p0A = sa->p0;
-        ga.p0B = sbs->p0;
-        ga.expA = sa->expo;
-        ga.expB = sbs->expo;
-        SP_TRY(zero_chunk(ctx, &ga.zero_chunk));
-        ga.task = task;
-        ga.work_ij = work_ij;
-        ga.work_out = work_out;
-        ga.work_off = work_off;
-        ga.nb = nb;
-        ga.mode = mode;
-        ga.mapX = mode ? A->d_map : nullptr;
-        ga.tilesX = mode ? A->d_tiles : nullptr;
-        ga.tilesC = C->d_tiles;
-        ga.normC = C->d_norm;
-        ga.part_fro2 = parts;
-        ga.part_trace = parts + 2 * nw;
-        ga.part_idem2 = parts + 4 * nw;
-        ga.status = &sc->status;
-        {
-            std::lock_guard<std::mutex> lock(g_mixed_init);
-            if (!g_attr_set[ctx->device]) {
-                for (int h = 4; h <= MX_LMAX_MAIN; ++h)
-                    SP_CUDA(cudaFuncSetAttribute(gemm_mixed_kernel(2, h),
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
-                for (int h = MX_LMAX_MAIN + 1; h <= MIXED_LMAX; ++h)
-                    SP_CUDA(cudaFuncSetAttribute(gemm_mixed_kernel(MX_LMAX_MAIN + 1, h),
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, GM_SMEM));
-                g_attr_set[ctx->device] = true;
-            }
-        }
+        SP_TRY(set_pass_attributes(ctx));
+        TileArgs ta;
+        memset(&ta, 0, sizeof ta);
+        ta.pairA = sa->pairs;
+        ta.pairB = sbs->pairs;
+        ta.expA = sa->expo;
+        ta.expB = sbs->expo;
+        ta.task = task;
+        ta.work_ij = work_ij;
+        ta.work_out = work_out;
+        ta.work_off = work_off;
+        ta.nb = nb;
+        ta.np = np;
+        ta.mode = mode;
+        ta.mapX = mode ? A->d_map : nullptr;
+        ta.tilesX = mode ? A->d_tiles : nullptr;
+        ta.tilesC = C->d_tiles;
+        ta.normC = C->d_norm;
+        ta.part_fro2 = parts;
+        ta.part_trace = parts + 4 * nw;
+        ta.part_idem2 = parts + 8 * nw;
+        ta.status = &sc->status;
         SP_CUDA(cudaMemsetAsync(&sc->status, 0, sizeof(int32_t), s));
         cudaEventRecord(ctx->ev[EV_PLAN1], s);
-        // levels above 9 do not fit in TMEM next to levels 2..9: a first pass forms them
-        // and leaves their (tiny) raw product in the output slots, the main pass adds it
-        auto window_for = [](int top) {
-            const double per = ldexp(1.0, 18) * (top + 1 > 4 ? top + 1 : 4);
-            return (int)floor((ldexp(1.0, 24) - 1.0) / per);
-        };
-        const int main_hi = lmax < MX_LMAX_MAIN ? lmax : MX_LMAX_MAIN;
-        if (lmax > main_hi) {
-            MixedArgs gb = ga;
-            gb.lv_lo = main_hi + 1;
-            gb.lv_hi = lmax;
-            gb.window = window_for(lmax);
-            gb.raw_out = 1;
-            gb.add_prev = 0;
+        // passes over levels 6..min(L, 9), 10..L, then 2..min(L, 5); the first ones
+        // leave their raw products in the output slots, each later one adds them, and
+        // the last (the largest terms) runs the SP2 epilogue
+        int ranges[3][2];
+        int npass = 0;
+        if (lmax >= 6) {
+            ranges[npass][0] = 6;
+            ranges[npass][1] = lmax < 9 ? lmax : 9;
+            ++npass;
+        }
+        if (lmax >= 10) {
+            ranges[npass][0] = 10;
+            ranges[npass][1] = lmax;
+            ++npass;
+        }
+        ranges[npass][0] = 2;
+        ranges[npass][1] = lmax < 5 ? lmax : 5;
+        ++npass;
+        for (int ps = 0; ps < npass; ++ps) {
+            const int lo = ranges[ps][0], hi = ranges[ps][1];
+            const PassKernel k = pass_kernel(lo, hi);
+            // exact f32 window: per leaf product a level sum is below 2^18 max(hi + 1, 4)
+            const double per = ldexp(1.0, 18) * (hi + 1 > 4 ? hi + 1 : 4);
+            ta.window = (int)floor((ldexp(1.0, 24) - 1.0) / per);
+            ta.raw_out = ps + 1 < npass ? 1 : 0;
+            ta.add_prev = ps > 0 ? 1 : 0;
             ++ctx->launches;
-            gemm_mixed_kernel(gb.lv_lo, gb.lv_hi)<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(gb);
+            k.fn<<<(unsigned)n_work, GM_THREADS, k.smem, s>>>(ta);
             SP_CHECK_LAUNCH();
         }
-        ga.lv_lo = 2;
-        ga.lv_hi = main_hi;
-        ga.window = window_for(main_hi);
-        ga.raw_out = 0;
-        ga.add_prev = lmax > main_hi ? 1 : 0;
-        ++ctx->launches;
-        gemm_mixed_kernel(ga.lv_lo, ga.lv_hi)<<<(unsigned)n_work, GM_THREADS, GM_SMEM, s>>>(ga);
-        SP_CHECK_LAUNCH();
         cudaEventRecord(ctx->ev[EV_GEMM1], s);
-        st = reduce_partials(ctx, parts, parts + 2 * nw, parts + 4 * nw, 2 * n_work);
+        st = reduce_partials(ctx, parts, parts + 4 * nw, parts + 8 * nw, 4 * n_work);
+        unsigned long long hf[2];
+        if (st == SPAMM_OK) {
+            SP_CUDA(cudaMemcpyAsync(hf, &sc->mx_formed, 16, cudaMemcpyDeviceToHost, s));
+            SP_CUDA(cudaStreamSynchronize(s));
+            *n_formed = (int64_t)hf[0];
+            *n_pairs_out = (int64_t)hf[1];
+        }
     } else {
         cudaEventRecord(ctx->ev[EV_PLAN1], s);
         SP_CUDA(cudaMemsetAsync(&sc->fro2, 0, 3 * sizeof(double), s));
         cudaEventRecord(ctx->ev[EV_GEMM1], s);
     }
     dfree(cnt, s); dfree(wf, s); dfree(of, s); dfree(toff, s); dfree(widx, s); dfree(oidx, s);
-    dfree(pc, s); dfree(pwf, s); dfree(ptoff, s); dfree(pwidx, s); dfree(d_tot, s);
+    dfree(d_tot, s);
     dfree(work_ij, s); dfree(work_out, s); dfree(work_off, s); dfree(task, s); dfree(parts, s);
     if (st != SPAMM_OK) {
         spamm_mat_free(C);

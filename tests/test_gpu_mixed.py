@@ -63,11 +63,16 @@ def test_mixed_tau_within_bound_and_close_to_oracle(gctx, orc, n, kind, seed):
         c = C.to_numpy()
         err = np.linalg.norm(c - A @ B)
         assert err <= rep["bound"] + fp64_noise
-        # the slicing error is charged: mixed vs float64 SpAMM at the same tau
-        assert np.linalg.norm(c - Cf.to_numpy()) <= rep["bound_round"] + fp64_noise
-        assert _rel(c, ref) <= 1e-13
+        # the mixed form forms every stored product of a 2 x 2 block tile once one of
+        # them reaches tau, so it skips a subset of what the float64 form (and the
+        # oracle) skip: both lie within their bounds of A B
+        both = rep["bound"] + repf["bound"] + 2 * fp64_noise
+        assert np.linalg.norm(c - Cf.to_numpy()) <= both
+        assert np.linalg.norm(c - ref) <= both
         assert rep["kept"] == repf["kept"]
-        assert rep["bound"] >= repf["bound"] and rep["bound_round"] > 0
+        assert rep["formed"] >= repf["formed"]
+        # the charge-only bound (everything formed) is the bound's floor
+        assert rep["bound"] >= rep["bound_round"] > 0
 
 
 @pytest.mark.parametrize("n,delta", [(512, 1e-6), (768, 1e-9), (1024, 1e-11)])
@@ -83,7 +88,9 @@ def test_mixed_delta_certified(gctx, orc, n, delta):
     assert np.linalg.norm(c - exact) < delta + fp64_noise
     assert rep["lmax"] >= 2
     Cf, repf = gctx.multiply(G, G, delta, prec="fp64")
-    assert abs(rep["tau_index"] - repf["tau_index"]) <= 3
+    # the mixed form forms whole 2 x 2 tiles and charges its slicing, so it may need a
+    # few table entries more (or many fewer) than the float64 form
+    assert rep["tau_index"] <= repf["tau_index"] + 8
 
 
 @pytest.mark.parametrize("branch", [0, 1])
