@@ -542,6 +542,14 @@ constexpr int SMEM_BUDGET = 220 * 1024;
 // Stage layout of a pass over levels LO..HI: the slices 1..SMAX of the A and of the B
 // pair tile for one K chunk, each [slice][half][2 KB] (the M = 128 and N = 128
 // operand orders). SMAX = HI - 1 (at most 9) is the highest slice any pair uses.
+// A task takes part in the pass over levels LO..HI when its lowest level pa + qb is
+// at most HI (tiles of small blocks, whose digits start late, form no pair of the
+// lowest levels). Producer and MMA warp skip the other tasks alike.
+template <int HI>
+__device__ __forceinline__ bool task_active(int pq) {
+    return (pq & 0xff) + (pq >> 8) <= HI;
+}
+
 template <int LO, int HI>
 struct PassShape {
     static constexpr int SMAX = HI - 1 < MX_S ? HI - 1 : MX_S;
@@ -635,6 +643,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
                 const int32_t jA = __shfl_sync(0xffffffffu, pA, j);
                 const int32_t jB = __shfl_sync(0xffffffffu, pB, j);
                 const int jpq = __shfl_sync(0xffffffffu, pq, j);
+                if (!task_active<HI>(jpq)) continue;
                 const int pa = jpq & 0xff, qb = jpq >> 8;
                 const int pmax = min(SMAX, HI - qb), qmax = min(SMAX, HI - pa);
                 const int np = pmax >= pa ? pmax - pa + 1 : 0;
@@ -678,6 +687,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
         int it = 0;
         int64_t t = t0;
         bool ok = true;
+        int32_t pq_batch = 0;   // first slices of 32 tasks, one per lane
         for (int win = 0; win < nwin && ok; ++win) {
             ok = __all_sync(0xffffffffu, tc::mbar_wait(b_acce, win & 1, WAIT_LIMIT));
             if (!ok) {
@@ -687,6 +697,12 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
             tc::fence_after();
             const int64_t tend = min(t1, t + a.window);
             for (; t < tend && ok; ++t) {
+                if (((t - t0) & 31) == 0) {
+                    const int64_t tl = t + lane;
+                    pq_batch = tl < t1 ? a.task[3 * tl + 2] : 0;
+                }
+                if (!task_active<HI>(__shfl_sync(0xffffffffu, pq_batch, (int)((t - t0) & 31))))
+                    continue;
                 for (int c = 0; c < KCH; ++c, ++it) {
                     const int st = it % NST;
                     ok = __all_sync(0xffffffffu,
