@@ -212,7 +212,7 @@ void plan_free(Plan* plan, cudaStream_t s);
 // blocks; ch->lmax > 0 applies the mixed keep rule (charge below the norm product)
 int plan_count_blocks(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
                       const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
-                      int sym, const ChargeData* ch, int32_t* cnt, int32_t* wf, int32_t* of);
+                      int sym, int32_t* cnt, int32_t* wf, int32_t* of);
 // mapC[b] = out slot for every flagged block, and the slot -> block coordinates
 int plan_write_out_map(spamm_ctx* ctx, const int32_t* of, const int64_t* oidx, int nb,
                        spamm_mat* C);

@@ -1,32 +1,29 @@
 // Mixed-precision leaf products: float64-accurate products of float64 leaf
-// blocks on the bf16 tensor cores (tcgen05), with the rounding of every kept
+// blocks on the bf16 tensor cores (tcgen05), with the rounding of every formed
 // product charged inside the Algorithm 3 bound.
 //
 // Slicing. Every row r of the left operand gets an exponent e_r with
-// max_c |A[r,c]| < 2^e_r (every column s of the right operand an f_s). An
-// entry becomes signed 7-bit digits: r_0 = A[r,c] / 2^e_r, and for p = 1..8
-// a_p = rint(128 r_{p-1}), r_p = 128 r_{p-1} - a_p, so that
-//     A = sum_p A_p + T_8,  A_p[r,c] = a_p 2^(e_r - 7p),  |a_1| <= 128, |a_p| <= 64,
-// every digit exact in bf16. The slices are stored per leaf block in the
-// K-major, no-swizzle layout that the tensor core reads (8-row x 16-byte core
-// matrices), so a 2 KB chunk (64 rows x 16 K) moves with one bulk copy.
+// max_c |A[r,c]| < 2^e_r (every column s of the right operand an f_s). An entry
+// becomes 9 balanced base-128 digits of V = round(x 2^(63 - e_r)), formed exactly
+// from the float64 bits:
+//     A = sum_{p=1..9} A_p + T_9,  A_p[r,c] = d_p 2^(e_r - 7p),  |d_1| <= 128, |d_p| <= 64,
+// every digit exact in bf16. The slices are stored in pair tiles (two blocks of
+// adjacent block rows, or block columns) in the K-major, no-swizzle layout the
+// tensor core reads (8-row x 16-byte core matrices).
 //
 // Exact accumulation. Products of digits are integers below 2^14 in units of
-// 2^(e_r + f_s - 7(p+q)); grouping them by level L = p + q, one level's sum over
-// one leaf product (K = 64) stays below 2^18 (L + 1) <= 2^21.3 for L <= 9, so
-// T = 6 leaf products fit below 2^24 and the f32 accumulators hold them
-// exactly. Every T products the 8 level accumulators (all 512 TMEM columns)
-// are folded into two int64 words per entry, V = H 2^28 + Lo with
-// V = sum_L G_L 2^(7(Lmax - L)), and zeroed.
+// 2^(e_r + f_s - 7(p+q)); grouped by level L = p + q, one level's sum over one
+// leaf product (K = 64) stays below 2^18 max(L + 1, 4), so windows of 5-10 leaf
+// products keep the f32 accumulators below 2^24, hence exact. A pass over at most
+// four levels (4 x 128 TMEM columns) folds each window into one int64 per entry,
+// V = sum_L G_L 2^(7(HI - L)).
 //
-// Charge. Forming only the pairs p + q <= L leaves the error
-//     A B - sum_{p+q<=L} A_p B_q = sum_{p=1}^{L-1} A_p T^B_{L-p} + T^A_{L-1} B,
-// bounded by c = sum_p ||A_p||_F ||T^B_{L-p}||_F + ||T^A_{L-1}||_F ||B||_F per
-// product (slice and tail norms are kept per block). A kept triple contributes
-// min(c, ||A_ik|| ||B_kj||) to Algorithm 3's leaf in place of 0; when c is not
-// below the norm product the product is not formed at all (its error is then
-// at most the norm product). The recursion of Algorithm 3 is unchanged, so the
-// bound it returns covers skipped products and slicing together.
+// Charge. Forming only the pairs p + q <= L leaves, with m = min(L - 1, 9),
+//     sum_{p<=m} A_p (B - sum_{q<=min(L-p,9)} B_q) + (A - sum_{p<=m} A_p) B,
+// bounded per product by slice and tail norms (common.cuh: charge). The leaf-
+// product kernel forms whole 2 x 2 block tiles; Algorithm 3's leaf charges a formed
+// product its charge c and a skipped one max(p, c) (cse.cu). The recursion is
+// unchanged, so the bound it returns covers skipped products and slicing together.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -43,13 +40,11 @@ constexpr int MX_S = MX_SLICES;
 constexpr int MX_BS = 64;
 constexpr int CHUNK = 2048;                      // 64 rows x 16 K x 2 bytes
 constexpr int KCH = 4;                           // K chunks of 16 in a 64-wide block
-constexpr int TILE_BYTES = MX_S * KCH * CHUNK;   // all slices of one block (72 KB)
-// Slice storage is K-chunk-major, so that the slices p..p' of one K chunk are one
-// contiguous run and reach shared memory in a single bulk copy:
-//   block tile (B operand): [K chunk][slice p][2 KB]
-//   pair tile (A operand, block rows 2I and 2I+1 of one k): [K chunk][p][half][2 KB],
-//   which is also the shared-memory order of the M = 128 operand.
-constexpr int TILE_CSTRIDE = MX_S * CHUNK;
+// Slices are stored in pair tiles, K-chunk-major, so that the slices p..p' of one K
+// chunk are one contiguous run and reach shared memory in a single bulk copy:
+//   [K chunk][slice p][half][2 KB], half = block row 2I or 2I + 1 (block column 2J or
+//   2J + 1 for the transposed B operand): the shared-memory order of the M = 128 (or
+//   N = 128) operand.
 constexpr int PAIR_CSTRIDE = 2 * MX_S * CHUNK;
 constexpr int PAIR_BYTES = KCH * PAIR_CSTRIDE;   // 144 KB
 
@@ -108,11 +103,11 @@ __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __re
 // Slice norms are exact (digit squares summed exactly per row in f32); tail norms
 // are upper bounds: |R_p| per entry, plus 1/2 where the rounding of V was inexact,
 // summed in f32 and inflated by 2^-12 to cover the f32 rounding. transpose: slice the
-// transposed block with column exponents. The digits go to the block's tile (slices,
-// when given) and to its half of the pair tile (pairs, when given).
+// transposed block with column exponents. The digits go to the block's half of its
+// pair tile.
 __global__ void __launch_bounds__(256, 3)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
-        const int32_t* __restrict__ expo, uint8_t* __restrict__ slices, uint8_t* __restrict__ pairs,
+        const int32_t* __restrict__ expo, uint8_t* __restrict__ pairs,
         const int64_t* __restrict__ pair_idx, int8_t* __restrict__ p0, double* __restrict__ sn,
         double* __restrict__ tn) {
     const int64_t s = blockIdx.x;
@@ -138,13 +133,10 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
 #pragma unroll
     for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.f;
     int firstp = MX_S + 1;
-    uint8_t* out = slices ? slices + s * (int64_t)TILE_BYTES : nullptr;
-    uint8_t* pout = nullptr;
-    if (pairs) {
-        // pairing along block rows (transpose = 0) or block columns (transpose = 1)
-        const int r = transpose ? bj : bi, k = transpose ? bi : bj;
-        pout = pairs + pair_idx[(int64_t)(r >> 1) * nb + k] * (int64_t)PAIR_BYTES + (r & 1) * CHUNK;
-    }
+    // pairing along block rows (transpose = 0) or block columns (transpose = 1)
+    const int pr = transpose ? bj : bi, pk = transpose ? bi : bj;
+    uint8_t* pout =
+        pairs + pair_idx[(int64_t)(pr >> 1) * nb + pk] * (int64_t)PAIR_BYTES + (pr & 1) * CHUNK;
 #pragma unroll
     for (int g2 = 0; g2 < 2; ++g2) {
         const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
@@ -200,10 +192,7 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
         for (int p = 0; p < MX_S; ++p) {
             const int within = (row >> 3) * 256 + (kg & 1) * 128 + (row & 7) * 16;
             const uint4 v = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
-            if (out)
-                *reinterpret_cast<uint4*>(out + (kg >> 1) * TILE_CSTRIDE + p * CHUNK + within) = v;
-            if (pout)
-                *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
+            *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
         }
     }
     // per-row sums -> scale by 2^(2(e_r - 7p)) (slice) or 2^(2(e_r - 63)) (tail) -> block sums
@@ -235,7 +224,6 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
 }
 
 struct SliceSet {
-    uint8_t* slices = nullptr;
     uint8_t* pairs = nullptr;       // pair tiles (A operand)
     int64_t* pair_idx = nullptr;    // [(nb + 1) / 2 * nb]: pair tile of (I, k), or -1
     int8_t* p0 = nullptr;
@@ -243,7 +231,6 @@ struct SliceSet {
     double* tn = nullptr;
     int32_t* expo = nullptr;
     void free(cudaStream_t s) {
-        dfree(slices, s);
         dfree(pairs, s);
         dfree(pair_idx, s);
         dfree(p0, s);
@@ -294,14 +281,12 @@ __global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb, int
     }
 }
 
-// Slices of X: block tiles when want_tiles, pair tiles when want_pairs (pairs of block
-// rows, or of block columns when transpose).
-static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, int want_tiles,
-                        int want_pairs, SliceSet* out) {
+// Slices of X into pair tiles: pairs of block rows, or of block columns when
+// transpose (the right operand, sliced with column exponents).
+static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, SliceSet* out) {
     cudaStream_t s = ctx->stream;
     const int64_t ns = X->nslots > 0 ? X->nslots : 1;
-    if (want_tiles) SP_TRY(dalloc((void**)&out->slices, (size_t)ns * TILE_BYTES, s));
-    if (want_pairs) {
+    {
         const int nb = X->nb;
         const int64_t ne = (int64_t)((nb + 1) / 2) * nb;
         int32_t* flag = nullptr;
@@ -345,8 +330,8 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, int w
     if (X->nslots > 0) {
         ++ctx->launches;
         k_split<<<(unsigned)X->nslots, 256, 0, s>>>(X->d_tiles, X->d_coord, X->nb, transpose,
-                                                    out->expo, out->slices, out->pairs,
-                                                    out->pair_idx, out->p0, out->sn, out->tn);
+                                                    out->expo, out->pairs, out->pair_idx,
+                                                    out->p0, out->sn, out->tn);
     }
     SP_CHECK_LAUNCH();
     dfree(rmax, s);
@@ -941,8 +926,8 @@ int mixed_prepare(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, int sy
     // pair tiles over block rows of A; over block columns of B (transposed split). A
     // symmetric X serves as its own B operand: the pair tile (J, k) of X holds the
     // blocks (k, 2J), (k, 2J + 1) of X in the B operand's K-major order.
-    int st = split_matrix(ctx, A, 0, 0, 1, sa);
-    if (st == SPAMM_OK && !sym) st = split_matrix(ctx, B, 1, 0, 1, sb);
+    int st = split_matrix(ctx, A, 0, sa);
+    if (st == SPAMM_OK && !sym) st = split_matrix(ctx, B, 1, sb);
     mp->sa = sa;
     mp->sb = sb;
     mp->sym = sym;

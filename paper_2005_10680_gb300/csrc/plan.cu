@@ -24,7 +24,7 @@ namespace spamm {
 __global__ void k_plan_count(const int32_t* __restrict__ mapA, const double* __restrict__ nA,
                              const int32_t* __restrict__ mapB, const double* __restrict__ nB,
                              const int32_t* __restrict__ mapX, int nb, int mode_dbl, int sym,
-                             ChargeData ch, const double* __restrict__ d_tau,
+                             const double* __restrict__ d_tau,
                              int32_t* __restrict__ cnt,
                              int32_t* __restrict__ work_flag, int32_t* __restrict__ out_flag,
                              unsigned long long* __restrict__ n_cand) {
@@ -42,10 +42,6 @@ __global__ void k_plan_count(const int32_t* __restrict__ mapA, const double* __r
             ++cand;
             const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
             if (p < tau) continue;
-            // mixed rule: a product is formed only when its charge is below its norm product
-            if (ch.lmax > 0 &&
-                !(charge(ch, sa, charge_bslot(ch, k, j), nB[(int64_t)k * nb + j]) < p))
-                continue;
             ++kept;
         }
         const int hx = mapX ? (mapX[b] >= 0) : 0;
@@ -122,14 +118,14 @@ __global__ void k_write_out_map(const int32_t* __restrict__ of, const int64_t* _
 
 int plan_count_blocks(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
                       const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
-                      int sym, const ChargeData* ch, int32_t* cnt, int32_t* wf, int32_t* of) {
+                      int sym, int32_t* cnt, int32_t* wf, int32_t* of) {
     DevScalars* sc = (DevScalars*)ctx->d_scalars;
     const int nb = A->nb;
     const int64_t nb2 = (int64_t)nb * nb;
     const unsigned G = (unsigned)((nb2 + 255) / 256);
     ++ctx->launches;
     k_plan_count<<<G, 256, 0, ctx->stream>>>(A->d_map, nA, B->d_map, nB, X ? X->d_map : nullptr,
-                                             nb, mode_dbl, sym, ch ? *ch : ChargeData(), d_tau,
+                                             nb, mode_dbl, sym, d_tau,
                                              cnt, wf, of, &sc->n_cand);
     SP_CHECK_LAUNCH();
     return SPAMM_OK;
@@ -184,7 +180,7 @@ int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, cons
     SP_CUDA(cudaMemsetAsync(&sc->n_cand, 0, 2 * sizeof(unsigned long long), s));
     const int T = 256;
     const unsigned G = (unsigned)((nb2 + T - 1) / T);
-    SP_TRY(plan_count_blocks(ctx, A, B, nA, nB, d_tau, X, mode_dbl, sym, nullptr, cnt, wf, of));
+    SP_TRY(plan_count_blocks(ctx, A, B, nA, nB, d_tau, X, mode_dbl, sym, cnt, wf, of));
     SP_TRY(scan_i32_to_i64(ctx, cnt, toff, nb2, &sc->n_tasks));
     unsigned long long* d_nwork = nullptr;
     SP_TRY(dalloc((void**)&d_nwork, sizeof(unsigned long long), s));
