@@ -813,7 +813,12 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
             for (int j = 0; j < 32; ++j) {
                 const int sc = sc0 + j;
                 const int fs = a.expB[bj * MX_BS + sc];
-                double cv = ldexp((double)acc[j], er + fs - MX_W * HI);
+                // V 2^e: a multiply by the power of two when 2^e is a normal double
+                const int ex = er + fs - MX_W * HI;
+                const double vf = (double)acc[j];
+                double cv = (ex >= -1022 && ex <= 1023)
+                                ? vf * __longlong_as_double((long long)(ex + 1023) << 52)
+                                : ldexp(vf, ex);
                 if (a.add_prev && Co) cv += Co[rr * MX_BS + sc];
                 if (a.raw_out) {
                     if (Co) Co[rr * MX_BS + sc] = cv;
