@@ -347,7 +347,7 @@ def run_ours(args, rank, world):
                 "algorithmic": "2*bs^3 flop per formed leaf product"}
     else:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        roof = {"bound": "tensor", "kernel": "k_gemm_mixed", "peak": peaks["bf16_tflops_sustained"],
+        roof = {"bound": "tensor", "kernel": "k_gemm_tile", "peak": peaks["bf16_tflops_sustained"],
                 "unit": "TFLOP/s", "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured)",
                 "algorithmic": "2*128*128*64 flop per (p,q) bf16 slice pair of a 128x128 tile task (4 MMAs of 128x128x16)"}
     achieved = pipe / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0

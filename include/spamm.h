@@ -44,8 +44,9 @@ typedef struct spamm_mat spamm_mat;
 
 /* Leaf-product arithmetic. FP64: every kept leaf product in float64.
    MIXED: leaf products on the bf16 tensor cores via exact fixed-point
-   slices; the slicing error is bounded per kept product and charged inside
-   the Algorithm 3 bound, so the certified bound still covers the result. */
+   slices (bs = 64 only). Products are formed per 2 x 2 block tile, a superset of
+   the kept set. The slicing error of every formed product is bounded and charged
+   inside the Algorithm 3 bound, so the certified bound still covers the result. */
 typedef enum { SPAMM_FP64 = 0, SPAMM_MIXED = 1 } spamm_prec;
 
 /* Purification variants, numbered as the paper's algorithms:
@@ -64,15 +65,17 @@ typedef struct {
     int32_t cse_evals;     /* Algorithm 3 evaluations run by the tau search */
     double bound;          /* certified ||SpAMM(A,B,tau) - AB||_F bound (Alg. 3), incl. bound_round */
     double bound_round;    /* mixed form: Algorithm 3 bound of the slicing charges alone
-                              (every product kept); 0 for float64 leaf products */
+                              (every product formed); 0 for float64 leaf products */
     int32_t lmax;          /* mixed form: highest slice level p + q formed; 0 = float64 */
     int32_t reserved;
     int64_t candidates;    /* leaf triples (i,k,j) with A_ik and B_kj both present */
     int64_t kept;          /* kept leaf triples of the product (p >= tau) */
-    int64_t formed;        /* leaf products multiplied: == kept, except SP2 steps, which form
-                              blocks i <= j only and mirror them (X symmetric) */
+    int64_t formed;        /* leaf products multiplied. FP64: == kept, except SP2 steps, which
+                              form blocks i <= j only and mirror them (X symmetric). Mixed:
+                              every stored product of each triggered 2 x 2 block tile */
     double pipe_flops;     /* arithmetic issued by the leaf-product kernel: 2 bs^3 per formed
-                              product (FP64), or 2*128*64*64 per (p,q) slice pair (mixed) */
+                              product (FP64), or 2*128*128*64 per (p,q) slice pair of a tile
+                              task (mixed) */
     int64_t nnzb_out;      /* leaf blocks in the result */
     double fro_out;        /* ||result||_F */
     double trace_out;      /* trace of the result */
