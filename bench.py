@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--protocol", action="store_true",
                     help="run the two-squares experiment instead of the purification bench")
     ap.add_argument("--deltas", default="1e-2,1e-4,1e-6,1e-8")
+    ap.add_argument("--bound", default="alg3", choices=["alg3", "flat"],
+                    help="error bound of the tau searches (Algorithm 3, or the flat bound)")
     ap.add_argument("--input-cache", default=None,
                     help="npz file holding the generated input (written when absent)")
     return ap.parse_args()
@@ -275,6 +277,7 @@ def run_ours(args, rank, world):
     D_host = torch.empty((n, n), dtype=torch.float64).pin_memory()
     stream = torch.cuda.Stream()
     ctx = sp.Context(local, stream=stream)
+    ctx.set_bound(args.bound)
     form = args.form
     if form == "auto":
         form = "mixed" if ctx.supports("mixed", bs) else "fp64"
@@ -362,7 +365,7 @@ def run_ours(args, rank, world):
             "dtype": "f64" if form == "fp64" else "bf16 slices (f32 accumulate) -> f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "bs": bs, "eps": args.eps,
-                       "variant": args.variant, "form": form,
+                       "variant": args.variant, "form": form, "bound": args.bound,
                        "l2": "inputs larger than L2 (2.1 GB per matrix), no flush",
                        "parallelism": f"replicas x{world}"},
             "spamm_ms": spamm_ms,
@@ -463,18 +466,19 @@ def run_protocol(args):
     stream = torch.cuda.Stream()
     ctx = sp.Context(0, stream=stream)
     fastest = "mixed" if ctx.supports("mixed", args.bs) else "fp64"
-    forms = [args.form] if args.form != "auto" else sorted({fastest, "fp64"})
     F = ctx.from_dense(torch.from_numpy(P.F), bs=args.bs)
     D, rep = ctx.purify(F, P.n_occ, args.eps, args.n_iter, P.homo, P.lumo,
                         variant=args.variant, prec=fastest, strict=False)
     del F
+    ctx.set_bound(args.bound)
+    forms = [args.form] if args.form != "auto" else sorted({fastest, "fp64"})
     for form in forms:
         for delta in [float(x) for x in args.deltas.split(",")]:
             for name, v in PROTOCOL_VARIANTS:
                 out = square_twice(ctx, D, delta, v, form)
                 line = {"protocol": "two squares of a converged D", "variant": name,
-                        "algorithm": v, "delta": delta, "form": form, "n": args.n,
-                        "bs": args.bs,
+                        "algorithm": v, "delta": delta, "form": form, "bound": args.bound,
+                        "n": args.n, "bs": args.bs,
                         "D": f"SP2 purification (Algorithm {args.variant}, {fastest}) of the "
                              f"bench's Fock matrix, eps {args.eps}, {rep['iters']} iterations"}
                 line.update(out)

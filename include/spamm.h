@@ -49,6 +49,16 @@ typedef struct spamm_mat spamm_mat;
    inside the Algorithm 3 bound, so the certified bound still covers the result. */
 typedef enum { SPAMM_FP64 = 0, SPAMM_MIXED = 1 } spamm_prec;
 
+/* Error bound used by the tau searches (and reported) on a context.
+   ALG3: Algorithm 3's hierarchical bound (the default).
+   FLAT: the one-level bound sqrt(sum_ij (sum_k e_ikj)^2) over the same leaf terms
+   e_ikj (a skipped product's norm product, a formed one's slicing charge). It is
+   still an upper bound on ||E||_F (triangle inequality per block) and never
+   exceeds Algorithm 3's (Minkowski's inequality), so it certifies at least as
+   large a tau. The paper's discussion of future work names it as a sharper
+   bound; it has no counterpart among the paper's algorithms. */
+typedef enum { SPAMM_BOUND_ALG3 = 0, SPAMM_BOUND_FLAT = 1 } spamm_bound;
+
 /* Purification variants, numbered as the paper's algorithms:
    1 = multiply exactly then truncate (Algorithm 1, "truncmul"),
    4 = SpAMM with error control only (Algorithm 4),
@@ -103,6 +113,11 @@ int64_t spamm_ctx_launches(const spamm_ctx* ctx);
 /* 1 when leaf products in precision `prec` with leaf size `bs` are built for
    the context's device, else 0. */
 int spamm_prec_supported(const spamm_ctx* ctx, spamm_prec prec, int bs);
+
+/* Select the bound for all later searches and bound evaluations on ctx (spamm_cse,
+   spamm_multiply, spamm_sp2_step, spamm_purify). SPAMM_EINVAL for an unknown
+   value. */
+int spamm_set_bound(spamm_ctx* ctx, spamm_bound bound);
 
 /* --------------------------------------------------------------- matrices */
 

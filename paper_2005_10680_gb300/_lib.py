@@ -109,6 +109,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_purify": ([vp, vp, i64, d, i32, P(PurifyOpts), P(vp), P(PurifyReport)], i32),
         "spamm_cse_search_noalloc": ([vp, vp, i64, d, vp, vp, vp, vp], i32),
         "spamm_autotune": ([vp, vp, d, i32, P(TuneResult)], i32),
+        "spamm_set_bound": ([vp, i32], i32),
         "spamm_purify_batched": ([vp, i32, P(vp), P(i64), d, i32, P(PurifyOpts), i32, P(vp),
                                   P(PurifyReport), P(ctypes.c_int32)], i32),
     }
@@ -378,3 +379,7 @@ class Context:
         return {"bs": r.bs, "prec": "mixed" if r.prec == MIXED else "fp64",
                 "ms": {"fp64_bs32": r.ms[0], "fp64_bs64": r.ms[1], "fp64_bs128": r.ms[2],
                        "mixed_bs64": r.ms[3]}, "cached": bool(r.cached)}
+
+    def set_bound(self, bound: str = "alg3"):
+        """Bound for later searches on this context: "alg3" (Algorithm 3) or "flat"."""
+        _check(_lib.spamm_set_bound(self.handle, {"alg3": 0, "flat": 1}[bound]), "spamm_set_bound")

@@ -429,6 +429,15 @@ extern "C" int64_t spamm_ctx_launches(const spamm_ctx* c) {
     return c ? (int64_t)c->launches : 0;
 }
 
+extern "C" int spamm_set_bound(spamm_ctx* ctx, spamm_bound bound) {
+    if (!ctx || (bound != SPAMM_BOUND_ALG3 && bound != SPAMM_BOUND_FLAT)) {
+        set_error("spamm_set_bound: bad argument");
+        return SPAMM_EINVAL;
+    }
+    ctx->bound = bound;
+    return SPAMM_OK;
+}
+
 extern "C" int spamm_prec_supported(const spamm_ctx* c, spamm_prec prec, int bs) {
     if (!c || !(bs == 32 || bs == 64 || bs == 128)) return 0;
     if (prec == SPAMM_FP64) return 1;

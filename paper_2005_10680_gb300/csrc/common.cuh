@@ -51,6 +51,7 @@ struct spamm_ctx {
     // start, since the bound is monotone along both
     int hint_tau = -1;
     int hint_lmax = 0;
+    int bound = SPAMM_BOUND_ALG3;   // spamm_bound of the searches on this context
 };
 
 struct spamm_mat {

@@ -58,6 +58,94 @@ __device__ __forceinline__ double fold_levels(double* sh, int levels) {
     return sh[0];
 }
 
+// Algorithm 3's leaf term for the triple (i, k, j) at threshold tau (0 outside the
+// grid or for an absent block).
+__device__ __forceinline__ double leaf_value(const double* __restrict__ nA,
+                                             const double* __restrict__ nB, int nb,
+                                             const ChargeData& ch, double tau, int i, int k, int j) {
+    double v = 0.0;
+    if (i < nb && k < nb && j < nb) {
+        const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
+        if (p != 0.0) {
+            if (ch.lmax == 0) {
+                // float64 leaf products: Algorithm 3's leaf, p if skipped
+                v = p < tau ? p : 0.0;
+            } else {
+                // mixed form: the leaf-product kernel forms every stored product of
+                // a 2 x 2 block tile at k once some product of the tile reaches
+                // tau (its trigger: the largest one, the product of the pair
+                // maxima). A formed product is charged its slicing charge c, a
+                // skipped one max(p, c): its error is at most p, and the max keeps
+                // the bound non-increasing as tau decreases. A symmetric SP2 step
+                // writes the blocks below the diagonal tiles as transposes of
+                // blocks (j, i), whose products are (j, k, i): charge those.
+                const int i0 = i & ~1, j0 = j & ~1;
+                const double ra = fmax(nA[(int64_t)i0 * nb + k],
+                                       i0 + 1 < nb ? nA[(int64_t)(i0 + 1) * nb + k] : 0.0);
+                const double rb = fmax(nB[(int64_t)k * nb + j0],
+                                       j0 + 1 < nb ? nB[(int64_t)k * nb + j0 + 1] : 0.0);
+                const double m = ra * rb;
+                int ii = i, jj = j;
+                if (ch.bt_from_a && (i >> 1) > (j >> 1)) {
+                    ii = j;
+                    jj = i;
+                }
+                const int32_t sa = ch.mapA[(int64_t)ii * nb + k];
+                const int32_t sb = charge_bslot(ch, k, jj);
+                const double c = charge(ch, sa, sb, nB[(int64_t)k * nb + jj]);
+                v = m >= tau ? c : fmax(p, c);
+            }
+        }
+    }
+    return v;
+}
+
+// Flat (one-level) bound sqrt(sum_ij (sum_k leaf_ikj)^2): by the triangle inequality
+// per block it bounds the error as Algorithm 3 does, and by Minkowski's inequality it
+// never exceeds Algorithm 3's hierarchical value. One block per row i of C: per j the
+// k-sum in a fixed tree, then rows[i] = sum_j S_ij^2 in order of j.
+__global__ void __launch_bounds__(256) k_flat_rows(const double* __restrict__ nA,
+                                                   const double* __restrict__ nB, int nb,
+                                                   const double* __restrict__ d_tau, ChargeData ch,
+                                                   const int32_t* __restrict__ d_done,
+                                                   double* __restrict__ rows) {
+    if (d_done && *d_done) return;
+    __shared__ double sh[256];
+    const int i = blockIdx.x, t = threadIdx.x;
+    const double tau = *d_tau;
+    double row = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        double v = 0.0;
+        for (int k = t; k < nb; k += 256) v += leaf_value(nA, nB, nb, ch, tau, i, k, j);
+        sh[t] = v;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (t < o) sh[t] += sh[t + o];
+            __syncthreads();
+        }
+        if (t == 0) row = fma(sh[0], sh[0], row);
+        __syncthreads();
+    }
+    if (t == 0) rows[i] = row;
+}
+
+__global__ void __launch_bounds__(1024) k_flat_total(const double* __restrict__ rows, int nb,
+                                                     const int32_t* __restrict__ d_done,
+                                                     double* __restrict__ d_err) {
+    if (d_done && *d_done) return;
+    __shared__ double sh[1024];
+    const int t = threadIdx.x;
+    double v = 0.0;
+    for (int i = t; i < nb; i += 1024) v += rows[i];
+    sh[t] = v;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (t < o) sh[t] += sh[t + o];
+        __syncthreads();
+    }
+    if (t == 0) *d_err = sqrt(sh[0]);
+}
+
 // LEAF: values from norm maps; else: values from the previous level buffer.
 template <bool LEAF>
 __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restrict__ nB, int nb,
@@ -77,40 +165,7 @@ __global__ void k_cse_cube(const double* __restrict__ nA, const double* __restri
     const int j = J0 * c + cube_coord(t, 2, levels);
     double v = 0.0;
     if (LEAF) {
-        if (i < nb && k < nb && j < nb) {
-            const double tau = *d_tau;
-            const double p = nA[(int64_t)i * nb + k] * nB[(int64_t)k * nb + j];
-            if (p != 0.0) {
-                if (ch.lmax == 0) {
-                    // float64 leaf products: Algorithm 3's leaf, p if skipped
-                    v = p < tau ? p : 0.0;
-                } else {
-                    // mixed form: the leaf-product kernel forms every stored product of
-                    // a 2 x 2 block tile at k once some product of the tile reaches
-                    // tau (its trigger: the largest one, the product of the pair
-                    // maxima). A formed product is charged its slicing charge c, a
-                    // skipped one max(p, c): its error is at most p, and the max keeps
-                    // the bound non-increasing as tau decreases. A symmetric SP2 step
-                    // writes the blocks below the diagonal tiles as transposes of
-                    // blocks (j, i), whose products are (j, k, i): charge those.
-                    const int i0 = i & ~1, j0 = j & ~1;
-                    const double ra = fmax(nA[(int64_t)i0 * nb + k],
-                                           i0 + 1 < nb ? nA[(int64_t)(i0 + 1) * nb + k] : 0.0);
-                    const double rb = fmax(nB[(int64_t)k * nb + j0],
-                                           j0 + 1 < nb ? nB[(int64_t)k * nb + j0 + 1] : 0.0);
-                    const double m = ra * rb;
-                    int ii = i, jj = j;
-                    if (ch.bt_from_a && (i >> 1) > (j >> 1)) {
-                        ii = j;
-                        jj = i;
-                    }
-                    const int32_t sa = ch.mapA[(int64_t)ii * nb + k];
-                    const int32_t sb = charge_bslot(ch, k, jj);
-                    const double c = charge(ch, sa, sb, nB[(int64_t)k * nb + jj]);
-                    v = m >= tau ? c : fmax(p, c);
-                }
-            }
-        }
+        v = leaf_value(nA, nB, nb, ch, *d_tau, i, k, j);
     } else {
         v = in[((int64_t)i * in_side + k) * in_side + j];
     }
@@ -125,6 +180,18 @@ int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const do
                   const ChargeData& d_charge, double* buf0, double* buf1) {
     cudaStream_t s = ctx->stream;
     const int nb = A->nb;
+    if (ctx->bound == SPAMM_BOUND_FLAT) {
+        double* rows = nullptr;
+        SP_TRY(dalloc((void**)&rows, sizeof(double) * (nb > 0 ? nb : 1), s));
+        ++ctx->launches;
+        k_flat_rows<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, s>>>(nA, nB, nb, d_tau, d_charge,
+                                                                d_done, rows);
+        ++ctx->launches;
+        k_flat_total<<<1, 1024, 0, s>>>(rows, nb, d_done, d_err);
+        SP_CHECK_LAUNCH();
+        dfree(rows, s);
+        return SPAMM_OK;
+    }
     int side = A->NB;
     int L = 0;
     while ((1 << L) < side) ++L;
