@@ -477,7 +477,7 @@ def run_protocol(args):
             for name, v in PROTOCOL_VARIANTS:
                 out = square_twice(ctx, D, delta, v, form)
                 line = {"protocol": "two squares of a converged D", "variant": name,
-                        "algorithm": v, "delta": delta, "form": form, "bound": args.bound,
+                        "algorithm": v, "delta": delta, "form": form, "bound_kind": args.bound,
                         "n": args.n, "bs": args.bs,
                         "D": f"SP2 purification (Algorithm {args.variant}, {fastest}) of the "
                              f"bench's Fock matrix, eps {args.eps}, {rep['iters']} iterations"}
