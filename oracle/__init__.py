@@ -8,8 +8,8 @@ never imports the product path.
 What lives where:
 
 * ``oracle.c`` (built into ``_build/liboracle.so`` with gcc) -- the tau table,
-  the quadtree of Eq. 2, Algorithm 2 (SpAMM), Algorithm 3 (CSE), the tau
-  selection rule, the dense product and leaf norms.
+  the quadtree of Eq. 2, Algorithm 2 (SpAMM), Algorithm 3 (CSE), the one-level
+  (flat) bound, the tau selection rule, the dense product and leaf norms.
 * this file -- ctypes wrappers, block truncation with ||E||_F < delta (the
   unit rule below), and the SP2 purification driver in the three variants of
   Algorithms 1, 4 and 5.
@@ -76,6 +76,7 @@ def lib():
         _lib.or_spamm.argtypes = [i64, i64, pd, i64, pd, i64, d, pd, i64]
         _lib.or_spamm.restype = i64
         _lib.or_cse.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
+        _lib.or_flat_bound.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
         _lib.or_select_tau.argtypes = [pd, i32, d]
         _lib.or_select_tau.restype = i32
         _lib.or_dense_gemm.argtypes = [i64, pd, pd, pd]
@@ -116,6 +117,16 @@ def cse(A, B, bs: int, taus=None) -> np.ndarray:
     n = A.shape[0]
     err = np.zeros(len(taus))
     lib().or_cse(n, bs, _p(A), n, _p(B), n, _p(taus), len(taus), _p(err))
+    return err
+
+
+def flat_bound(A, B, bs: int, taus=None) -> np.ndarray:
+    """One-level bound sqrt(sum_ij (sum_k p_ikj [p_ikj < tau])^2) for every tau."""
+    A, B = _f64(A), _f64(B)
+    taus = tau_table() if taus is None else _f64(taus)
+    n = A.shape[0]
+    err = np.zeros(len(taus))
+    lib().or_flat_bound(n, bs, _p(A), n, _p(B), n, _p(taus), len(taus), _p(err))
     return err
 
 

@@ -20,6 +20,9 @@
  *   or_select_tau  -- the candidate whose bound is the largest one still
  *                     below delta (text after Algorithm 3).
  *   or_dense_gemm  -- C = A B by the definition (triple loop).
+ *   or_flat_bound  -- the one-level bound sqrt(sum_ij (sum_k p_ikj [p_ikj < tau])^2)
+ *                     over leaf norm products (the sharper bound the paper's
+ *                     discussion of future work points to), one entry per tau.
  *
  * Quadrant indexing: Algorithm 2 uses C_ij = A_i0 B_0j + A_i1 B_1j with the
  * first index the row half, so child[r][c] below is (row half r, column
@@ -267,4 +270,33 @@ void or_block_norms(int64_t n, int64_t bs, const double* X, int64_t ld, double* 
                 }
             out[bi * nb + bj] = sqrt(ss);
         }
+}
+
+/*
+ * One-level bound over leaf blocks: E(tau) = sqrt(sum_ij (sum_k s_ikj)^2) with
+ * s_ikj = ||A_ik||_F ||B_kj||_F when that product is below tau (skipped), else 0.
+ * Leaf norms as in or_block_norms (blocks past n are zero).
+ */
+void or_flat_bound(int64_t n, int64_t bs, const double* A, int64_t lda, const double* B,
+                   int64_t ldb, const double* tau, int N, double* errors) {
+    int64_t nb = (n + bs - 1) / bs;
+    double* na = (double*)malloc(sizeof(double) * nb * nb);
+    double* nbn = (double*)malloc(sizeof(double) * nb * nb);
+    or_block_norms(n, bs, A, lda, na);
+    or_block_norms(n, bs, B, ldb, nbn);
+    for (int t = 0; t < N; ++t) {
+        double total = 0.0;
+        for (int64_t i = 0; i < nb; ++i)
+            for (int64_t j = 0; j < nb; ++j) {
+                double sum = 0.0;
+                for (int64_t k = 0; k < nb; ++k) {
+                    double p = na[i * nb + k] * nbn[k * nb + j];
+                    if (p < tau[t]) sum += p;
+                }
+                total += sum * sum;
+            }
+        errors[t] = sqrt(total);
+    }
+    free(na);
+    free(nbn);
 }

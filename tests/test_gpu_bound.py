@@ -1,7 +1,6 @@
-"""The flat (one-level) bound: the GPU value equals the formula
-sqrt(sum_ij (sum_k p_ikj [p_ikj < tau])^2) written out in numpy over the same
-leaf norms, never exceeds Algorithm 3's bound, still bounds the true error, and
-so certifies a tau at least as large."""
+"""The flat (one-level) bound: the GPU value equals the oracle's
+sqrt(sum_ij (sum_k p_ikj [p_ikj < tau])^2), never exceeds Algorithm 3's bound,
+still bounds the true error, and so certifies a tau at least as large."""
 import numpy as np
 import pytest
 
@@ -27,6 +26,7 @@ def test_flat_bound_formula_and_order(orc, n, seed):
     e3 = ctx.cse(GA, GB, taus)
     ctx.set_bound("flat")
     ef = ctx.cse(GA, GB, taus)
+    np.testing.assert_allclose(ef, orc.flat_bound(A, B, 64, taus), rtol=1e-12, atol=0)
     NA, NB = GA.block_norms(), GB.block_norms()
     want = np.array([_flat(NA, NB, t) for t in taus])
     np.testing.assert_allclose(ef, want, rtol=1e-12, atol=0)

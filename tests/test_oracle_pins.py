@@ -314,3 +314,46 @@ def test_sp2_lattice_matches_eigendecomposition(orc, variant, gap_mode):
     assert np.linalg.norm(r.D @ r.D - r.D) < 1e-5
     # every per-step tolerance and the branch rule are what the driver says
     assert all(d > 0 for d in r.deltas)
+
+
+# ------------------------------------------------------------ flat bound
+
+def test_flat_bound_equals_algorithm3_at_one_level(orc):
+    # a 2 x 2 leaf grid is a single level of Algorithm 3, where its recursion is
+    # exactly the flat formula
+    g = synth.rng(21)
+    A = g.standard_normal((8, 8))
+    B = g.standard_normal((8, 8))
+    taus = np.array([0.0, 0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 1e9])
+    np.testing.assert_allclose(orc.flat_bound(A, B, 4, taus), orc.cse(A, B, 4, taus),
+                               rtol=1e-14, atol=0)
+
+
+def test_flat_bound_closed_forms(orc):
+    n = 16
+    J = np.ones((n, n))
+    I = np.eye(n)
+    # everything skipped (tau above every leaf product, bs = 1): J J has all
+    # entries n, so the bound is sqrt(n^2 n^2) = n^2 = ||J J||_F; I I keeps only
+    # the diagonal triples, sqrt(n) = ||I||_F
+    assert orc.flat_bound(J, J, 1, [2.0])[0] == pytest.approx(n * n, rel=1e-15)
+    assert orc.flat_bound(I, I, 1, [2.0])[0] == pytest.approx(np.sqrt(n), rel=1e-15)
+    # nothing skipped at tau = 0
+    assert orc.flat_bound(J, J, 1, [0.0])[0] == 0.0
+
+
+@pytest.mark.parametrize("n,bs,seed", [(32, 4, 1), (48, 8, 2), (64, 8, 3), (50, 4, 4)])
+def test_flat_bound_between_true_error_and_algorithm3(orc, n, bs, seed):
+    A = synth.random_decaying(n, seed, length=3.0)
+    B = synth.random_decaying(n, seed + 7, length=4.0)
+    taus = orc.tau_table()[::7]
+    flat = orc.flat_bound(A, B, bs, taus)
+    alg3 = orc.cse(A, B, bs, taus)
+    exact = A @ B
+    # Minkowski: the one-level sum never exceeds the hierarchical one
+    assert np.all(flat <= alg3 * (1 + 1e-13))
+    for t, f in zip(taus, flat):
+        C, _ = orc.spamm(A, B, float(t), bs)
+        assert np.linalg.norm(C - exact) <= f * (1 + 1e-12) + 1e-14
+    # non-increasing along the table
+    assert np.all(np.diff(flat) <= 0)
