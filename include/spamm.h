@@ -128,6 +128,17 @@ int spamm_set_bound(spamm_ctx* ctx, spamm_bound bound);
 int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, int64_t ld, int bs,
                          double drop_abs, int a_on_device, spamm_mat** out);
 
+/* Build a block-sparse matrix from a list of leaf blocks (the store of Eq. 2's
+   lowest level, given directly): nnzb blocks, block t at block row brow[t] and
+   block column bcol[t] (0 <= brow, bcol < ceil(n / bs), no pair twice; host
+   arrays), its bs x bs entries row-major at tiles + t * bs * bs (host or device
+   memory as `tiles_on_device` says; copied). Entries of a block that fall outside
+   the n x n matrix are set to zero. Blocks not listed are zero. bs must be 32, 64
+   or 128. SPAMM_EINVAL for a bad index, a repeated block or a bad size. */
+int spamm_mat_from_blocks(spamm_ctx* ctx, int64_t n, int bs, int64_t nnzb, const int32_t* brow,
+                          const int32_t* bcol, const double* tiles, int tiles_on_device,
+                          spamm_mat** out);
+
 /* Write the matrix densely into out (n x n, leading dimension ld), host or
    device memory as `out_on_device` says. */
 int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* out, int64_t ld,

@@ -97,6 +97,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_prec_supported": ([vp, i32, i32], i32),
         "spamm_mat_from_dense": ([vp, vp, i64, i64, i32, d, i32, P(vp)], i32),
         "spamm_mat_to_dense": ([vp, vp, vp, i64, i32], i32),
+        "spamm_mat_from_blocks": ([vp, i64, i32, i64, P(i32), P(i32), vp, i32, P(vp)], i32),
         "spamm_mat_info": ([vp, P(i64), P(i32), P(i64)], i32),
         "spamm_mat_block_norms": ([vp, vp, _PD], i32),
         "spamm_mat_block_map": ([vp, vp, _PI32], i32),
@@ -383,3 +384,21 @@ class Context:
     def set_bound(self, bound: str = "alg3"):
         """Bound for later searches on this context: "alg3" (Algorithm 3) or "flat"."""
         _check(_lib.spamm_set_bound(self.handle, {"alg3": 0, "flat": 1}[bound]), "spamm_set_bound")
+
+    def from_blocks(self, n: int, bs: int, brow, bcol, tiles) -> Matrix:
+        """Matrix from a list of leaf blocks: tiles[t] (bs x bs) at block (brow[t], bcol[t]).
+        tiles: numpy array (host) or CUDA torch tensor (device), float64, contiguous."""
+        brow = np.ascontiguousarray(brow, dtype=np.int32)
+        bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+        out = ctypes.c_void_p()
+        if _is_torch(tiles):
+            ptr, on_dev, keep = ctypes.c_void_p(tiles.data_ptr()), int(tiles.is_cuda), tiles
+        else:
+            keep = np.ascontiguousarray(tiles, dtype=np.float64)
+            ptr, on_dev = keep.ctypes.data_as(ctypes.c_void_p), 0
+        _check(_lib.spamm_mat_from_blocks(self.handle, int(n), int(bs), len(brow),
+                                          brow.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          bcol.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                          ptr, on_dev, ctypes.byref(out)), "spamm_mat_from_blocks")
+        del keep
+        return Matrix(self, out.value)

@@ -10,6 +10,8 @@
 #include <cstdarg>
 #include <cstring>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace spamm {
@@ -395,6 +397,88 @@ extern "C" int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, 
         return st;
     }
     SP_CUDA(cudaStreamSynchronize(s));
+    *out = m;
+    return SPAMM_OK;
+}
+
+// zero the entries of boundary blocks that lie outside the n x n matrix
+__global__ void k_zero_outside(double* __restrict__ tiles, const int32_t* __restrict__ coord,
+                               int nb, int bs, int64_t n) {
+    const int64_t s = blockIdx.x;
+    const int32_t cd = coord[s];
+    const int bi = cd / nb, bj = cd % nb;
+    const int64_t rmax = n - (int64_t)bi * bs, cmax = n - (int64_t)bj * bs;
+    if (rmax >= bs && cmax >= bs) return;
+    double* T = tiles + s * (int64_t)bs * bs;
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+        const int r = e / bs, c = e % bs;
+        if (r >= rmax || c >= cmax) T[e] = 0.0;
+    }
+}
+
+extern "C" int spamm_mat_from_blocks(spamm_ctx* ctx, int64_t n, int bs, int64_t nnzb,
+                                     const int32_t* brow, const int32_t* bcol, const double* tiles,
+                                     int tiles_on_device, spamm_mat** out) {
+    if (!ctx || !out || n <= 0 || !(bs == 32 || bs == 64 || bs == 128) || nnzb < 0 ||
+        (nnzb > 0 && (!brow || !bcol || !tiles))) {
+        set_error("spamm_mat_from_blocks: bad argument");
+        return SPAMM_EINVAL;
+    }
+    *out = nullptr;
+    const int64_t nb = (n + bs - 1) / bs;
+    if (nb > (1 << 20) || nnzb > nb * nb) {
+        set_error("spamm_mat_from_blocks: bad size");
+        return SPAMM_EINVAL;
+    }
+    std::vector<int32_t> map((size_t)(nb * nb), -1);
+    std::vector<int32_t> coord((size_t)(nnzb > 0 ? nnzb : 1));
+    for (int64_t t = 0; t < nnzb; ++t) {
+        const int64_t i = brow[t], j = bcol[t];
+        if (i < 0 || i >= nb || j < 0 || j >= nb) {
+            set_error("spamm_mat_from_blocks: block %lld at (%lld, %lld) is outside the %lld x %lld "
+                      "block grid", (long long)t, (long long)i, (long long)j, (long long)nb,
+                      (long long)nb);
+            return SPAMM_EINVAL;
+        }
+        int32_t& slot = map[(size_t)(i * nb + j)];
+        if (slot >= 0) {
+            set_error("spamm_mat_from_blocks: block (%lld, %lld) is listed twice", (long long)i,
+                      (long long)j);
+            return SPAMM_EINVAL;
+        }
+        slot = (int32_t)t;
+        coord[(size_t)t] = (int32_t)(i * nb + j);
+    }
+    SP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    spamm_mat* m = nullptr;
+    SP_TRY(mat_alloc(ctx, n, bs, nnzb, &m));
+    m->nslots = m->nnzb = nnzb;
+    int st = SPAMM_OK;
+    const size_t tile_bytes = sizeof(double) * (size_t)bs * bs;
+    if (cudaMemcpyAsync(m->d_map, map.data(), sizeof(int32_t) * map.size(),
+                        cudaMemcpyHostToDevice, s) != cudaSuccess)
+        st = SPAMM_ECUDA;
+    if (st == SPAMM_OK && nnzb > 0) {
+        if (cudaMemcpyAsync(m->d_coord, coord.data(), sizeof(int32_t) * (size_t)nnzb,
+                            cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(m->d_tiles, tiles, tile_bytes * (size_t)nnzb,
+                            tiles_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                            s) != cudaSuccess)
+            st = SPAMM_ECUDA;
+        if (st == SPAMM_OK && n % bs != 0) {
+            ++ctx->launches;
+            k_zero_outside<<<(unsigned)nnzb, 256, 0, s>>>(m->d_tiles, m->d_coord, (int)nb, bs, n);
+            if (cudaGetLastError() != cudaSuccess) st = SPAMM_ECUDA;
+        }
+    }
+    if (st == SPAMM_OK) st = mat_compute_norms(ctx, m);
+    if (st == SPAMM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SPAMM_ECUDA;
+    if (st != SPAMM_OK) {
+        if (st == SPAMM_ECUDA) set_error("spamm_mat_from_blocks: CUDA error");
+        spamm_mat_free(m);
+        return st;
+    }
     *out = m;
     return SPAMM_OK;
 }

@@ -244,3 +244,44 @@ def test_purify_matches_oracle_and_eigendecomposition(gctx, orc, variant, gap_mo
         assert rep["iters"] == ref.iters
         np.testing.assert_allclose(rep["deltas"], ref.deltas, rtol=1e-12)
         assert np.linalg.norm(got - ref.D) <= 1e-7
+
+
+@pytest.mark.parametrize("n,bs", [(300, 64), (256, 32), (520, 128)])
+def test_from_blocks_roundtrip(gctx, orc, n, bs):
+    g = synth.rng(n + bs)
+    X = synth.random_decaying(n, n, length=n / 10.0)
+    nb = -(-n // bs)
+    # a sparse block list in shuffled order; entries of the boundary blocks beyond n
+    # are given as garbage and must come back as zeros
+    pad = np.zeros((nb * bs, nb * bs))
+    pad[:n, :n] = X
+    keep = [(i, j) for i in range(nb) for j in range(nb) if (i + 2 * j) % 3 != 1]
+    order = g.permutation(len(keep))
+    brow = np.array([keep[t][0] for t in order], dtype=np.int32)
+    bcol = np.array([keep[t][1] for t in order], dtype=np.int32)
+    tiles = np.stack([pad[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs] for i, j in zip(brow, bcol)])
+    outside = np.zeros_like(tiles, dtype=bool)
+    for t, (i, j) in enumerate(zip(brow, bcol)):
+        rows = np.arange(bs) + i * bs >= n
+        cols = np.arange(bs) + j * bs >= n
+        outside[t] = rows[:, None] | cols[None, :]
+    tiles = np.where(outside, 7.0, tiles)
+    M = gctx.from_blocks(n, bs, brow, bcol, tiles)
+    want = np.zeros((n, n))
+    for i, j in keep:
+        want[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs] = pad[i * bs:(i + 1) * bs, j * bs:(j + 1) * bs][
+            :max(0, min(bs, n - i * bs)), :max(0, min(bs, n - j * bs))]
+    np.testing.assert_array_equal(M.to_numpy(), want)
+    np.testing.assert_allclose(M.block_norms(), orc.block_norms(want, bs), rtol=1e-14, atol=0)
+    assert M.nnzb == len(keep)
+
+
+def test_from_blocks_rejects_bad_lists(gctx):
+    import paper_2005_10680_gb300 as sp
+    t = np.zeros((2, 32, 32))
+    with pytest.raises(sp.SpammError):
+        gctx.from_blocks(64, 32, [0, 0], [1, 1], t)       # the same block twice
+    with pytest.raises(sp.SpammError):
+        gctx.from_blocks(64, 32, [0, 2], [0, 0], t)       # outside the 2 x 2 block grid
+    E = gctx.from_blocks(64, 32, [], [], np.zeros((0, 32, 32)))
+    assert E.nnzb == 0 and not E.to_numpy().any()
