@@ -35,7 +35,7 @@ extern "C" {
 #define SPAMM_ECUDA 3        /* a CUDA call failed; spamm_last_error() has its text */
 #define SPAMM_ETIMEOUT 4     /* a bounded device-side wait gave up */
 #define SPAMM_ENOTCONV 5     /* purification hit n_iter before the stop rule */
-#define SPAMM_ENOTSUP 6      /* parameter combination not supported by this build */
+#define SPAMM_ENOTSUP 6      /* parameter combination not supported (e.g. mixed form with bs != 64) */
 
 #define SPAMM_N_TAU 350      /* tau candidates: tau_1 = 1, tau_i = 0.9 tau_{i-1} */
 
