@@ -55,6 +55,21 @@ int time_candidate(spamm_ctx* ctx, const double* d_dense, int64_t n, int bs, spa
     return SPAMM_OK;
 }
 
+// stored tiles -> the dense leading m x m block (row-major, ld m); the caller zeroes it
+__global__ void k_gather_leading(const double* __restrict__ tiles, const int32_t* __restrict__ coord,
+                                 int nb, int bs, int64_t m, double* __restrict__ out) {
+    const int64_t s = blockIdx.x;
+    const int32_t cd = coord[s];
+    if (cd < 0) return;
+    const int64_t r0 = (int64_t)(cd / nb) * bs, c0 = (int64_t)(cd % nb) * bs;
+    if (r0 >= m || c0 >= m) return;
+    const double* T = tiles + s * (int64_t)bs * bs;
+    for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
+        const int64_t r = r0 + e / bs, c = c0 + e % bs;
+        if (r < m && c < m) out[r * m + c] = T[e];
+    }
+}
+
 }  // namespace
 
 extern "C" int spamm_autotune(spamm_ctx* ctx, const spamm_mat* X, double delta, int allow_mixed,
@@ -82,17 +97,19 @@ extern "C" int spamm_autotune(spamm_ctx* ctx, const spamm_mat* X, double delta, 
         }
     }
     const int64_t m = X->n < TUNE_MAX_N ? X->n : TUNE_MAX_N;
-    double* full = nullptr;
+    // the leading m x m principal block, densely, gathered straight from the stored
+    // tiles (no dense copy of the whole matrix)
     double* sub = nullptr;
-    SP_TRY(dalloc((void**)&full, sizeof(double) * (size_t)X->n * X->n, ctx->stream));
-    int st = spamm_mat_to_dense(ctx, X, full, X->n, 1);
-    if (st == SPAMM_OK) st = dalloc((void**)&sub, sizeof(double) * (size_t)m * m, ctx->stream);
-    if (st == SPAMM_OK &&
-        cudaMemcpy2DAsync(sub, sizeof(double) * m, full, sizeof(double) * X->n,
-                          sizeof(double) * m, m, cudaMemcpyDeviceToDevice,
-                          ctx->stream) != cudaSuccess)
+    int st = dalloc((void**)&sub, sizeof(double) * (size_t)m * m, ctx->stream);
+    if (st == SPAMM_OK && cudaMemsetAsync(sub, 0, sizeof(double) * (size_t)m * m, ctx->stream) !=
+                              cudaSuccess)
         st = SPAMM_ECUDA;
-    dfree(full, ctx->stream);
+    if (st == SPAMM_OK && X->nslots > 0) {
+        ++ctx->launches;
+        k_gather_leading<<<(unsigned)X->nslots, 256, 0, ctx->stream>>>(X->d_tiles, X->d_coord, X->nb,
+                                                                      X->bs, m, sub);
+        if (cudaGetLastError() != cudaSuccess) st = SPAMM_ECUDA;
+    }
     Entry e;
     e.bs = 64;
     e.prec = SPAMM_FP64;
