@@ -277,7 +277,8 @@ int spamm_autotune(spamm_ctx* ctx, const spamm_mat* X, double delta, int allow_m
    n, n_occ[i] and opts[i]; eps and n_iter shared) purified concurrently by
    `workers` host threads, each with its own CUDA stream on ctx's device, so the
    kernels of different problems overlap. Each problem follows spamm_purify
-   exactly (identical results). Outputs: D[i] (caller frees), reps[i] (optional;
+   exactly (identical results), with ctx's error bound (spamm_set_bound). Work
+   pending on ctx's stream is finished first. Outputs: D[i] (caller frees), reps[i] (optional;
    its step-log pointers are used as given), status[i] = spamm_purify's status.
    Returns SPAMM_OK when every problem returned SPAMM_OK or SPAMM_ENOTCONV,
    else the status of a failing problem. */

@@ -34,6 +34,10 @@ extern "C" int spamm_purify_batched(spamm_ctx* ctx, int count, const spamm_mat* 
     std::atomic<int> failed(0);
     std::vector<std::thread> pool;
     const int device = ctx->device;
+    const int bound = ctx->bound;
+    // the inputs were made on ctx's stream: finish that work before other streams read them
+    SP_CUDA(cudaSetDevice(device));
+    SP_CUDA(cudaStreamSynchronize(ctx->stream));
     for (int w = 0; w < workers; ++w) {
         pool.emplace_back([&, w]() {
             spamm_ctx* wc = nullptr;
@@ -41,6 +45,7 @@ extern "C" int spamm_purify_batched(spamm_ctx* ctx, int count, const spamm_mat* 
                 failed.fetch_add(1);
                 return;
             }
+            wc->bound = bound;   // the caller's choice of error bound
             for (;;) {
                 const int i = next.fetch_add(1);
                 if (i >= count) break;
