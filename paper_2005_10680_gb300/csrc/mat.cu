@@ -358,8 +358,12 @@ extern "C" int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, 
     double* staged = nullptr;
     if (!a_on_device) {
         SP_TRY(dalloc((void**)&staged, sizeof(double) * (size_t)n * n, s));
-        SP_CUDA(cudaMemcpy2DAsync(staged, sizeof(double) * n, a, sizeof(double) * ld,
-                                  sizeof(double) * n, n, cudaMemcpyHostToDevice, s));
+        if (ld == n)   // contiguous rows: one linear copy
+            SP_CUDA(cudaMemcpyAsync(staged, a, sizeof(double) * (size_t)n * n,
+                                    cudaMemcpyHostToDevice, s));
+        else
+            SP_CUDA(cudaMemcpy2DAsync(staged, sizeof(double) * n, a, sizeof(double) * ld,
+                                      sizeof(double) * n, n, cudaMemcpyHostToDevice, s));
         src = staged;
         ld = n;
     }
@@ -508,8 +512,12 @@ extern "C" int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* ou
     }
     SP_CHECK_LAUNCH();
     if (!out_on_device) {
-        SP_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * ld, staged, sizeof(double) * m->n,
-                                  sizeof(double) * m->n, m->n, cudaMemcpyDeviceToHost, s));
+        if (ld == m->n)   // contiguous rows: one linear copy
+            SP_CUDA(cudaMemcpyAsync(out, staged, sizeof(double) * (size_t)m->n * m->n,
+                                    cudaMemcpyDeviceToHost, s));
+        else
+            SP_CUDA(cudaMemcpy2DAsync(out, sizeof(double) * ld, staged, sizeof(double) * m->n,
+                                      sizeof(double) * m->n, m->n, cudaMemcpyDeviceToHost, s));
         dfree(staged, s);
     }
     SP_CUDA(cudaStreamSynchronize(s));
