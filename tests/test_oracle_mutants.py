@@ -26,6 +26,11 @@ MUTANTS = {
     "leaf_transposed": ("entry(cx->B, B->r0 + k, B->c0 + j)", "entry(cx->B, B->r0 + j, B->c0 + k)"),
     "tau_table": ("tau[i] = 0.9 * tau[i - 1];", "tau[i] = 0.9 * tau[i - 1] * (1.0 - 1e-9);"),
     "norm_no_sqrt": ("q->norm = sqrt(ss);", "q->norm = ss;"),
+    "flat_no_square": ("total += sum * sum;", "total += sum;"),
+    "flat_non_strict": ("if (p < tau[t]) sum += p;", "if (p <= tau[t]) sum += p;"),
+    "flat_no_sqrt": ("errors[t] = sqrt(total);", "errors[t] = total;"),
+    "flat_transposed_b": ("double p = na[i * nb + k] * nbn[k * nb + j];",
+                          "double p = na[i * nb + k] * nbn[j * nb + k];"),
 }
 
 
@@ -43,6 +48,7 @@ def _build(tmp_path, name, old, new):
     lib.or_spamm.argtypes = [i64, i64, pd, i64, pd, i64, d, pd, i64]
     lib.or_spamm.restype = i64
     lib.or_cse.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
+    lib.or_flat_bound.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
     return lib
 
 
@@ -69,6 +75,12 @@ def _pins_hold(lib) -> bool:
         lib.or_cse(A.shape[0], bs, _p(A), A.shape[0], _p(B), A.shape[0], _p(taus), len(taus), _p(e))
         return e
 
+    def flat(A, B, bs, taus):
+        A, B, taus = np.ascontiguousarray(A), np.ascontiguousarray(B), np.ascontiguousarray(taus, dtype=float)
+        e = np.zeros(len(taus))
+        lib.or_flat_bound(A.shape[0], bs, _p(A), A.shape[0], _p(B), A.shape[0], _p(taus), len(taus), _p(e))
+        return e
+
     A = np.array([[1.0, 2.0], [3.0, 4.0]])
     B = np.array([[5.0, 6.0], [7.0, 8.0]])
     if not np.array_equal(spamm(A, B, 15.5, 1), np.array([[0.0, 16.0], [28.0, 50.0]])):
@@ -83,15 +95,29 @@ def _pins_hold(lib) -> bool:
     J = np.ones((8, 8))
     if abs(cse(J, J, 1, [2.0])[0] - 64.0) > 1e-12:
         return False
+    # flat bound: closed forms, equal to Algorithm 3 at one level (2 x 2 leaves)
+    if abs(flat(J, J, 1, [2.0])[0] - 64.0) > 1e-12 or abs(flat(I, I, 1, [2.0])[0] - 2.0) > 1e-14:
+        return False
+    if flat(J, J, 1, [1.0])[0] != 0.0:          # products equal to tau are kept
+        return False
+    g = synth.rng(21)
+    A8, B8 = g.standard_normal((8, 8)), g.standard_normal((8, 8))
+    t8 = np.array([0.5, 2.0, 8.0, 1e9])
+    if not np.allclose(flat(A8, B8, 4, t8), cse(A8, B8, 4, t8), rtol=1e-14, atol=0):
+        return False
     for seed in (1, 2):
         X = synth.random_decaying(48, seed, length=3.0)
         Y = synth.random_decaying(48, seed + 7, length=5.0).T.copy()
         if np.linalg.norm(spamm(X, Y, 0.0, 8) - X @ Y) > 1e-12 * np.linalg.norm(X @ Y):
             return False
         b = cse(X, Y, 8, tau)
+        f = flat(X, Y, 8, tau)
         for k in range(0, 350, 25):
-            if np.linalg.norm(X @ Y - spamm(X, Y, tau[k], 8)) > b[k] * (1 + 1e-12) + 1e-13:
+            err = np.linalg.norm(X @ Y - spamm(X, Y, tau[k], 8))
+            if err > b[k] * (1 + 1e-12) + 1e-13 or err > f[k] * (1 + 1e-12) + 1e-13:
                 return False
+        if np.any(f > b * (1 + 1e-13)):
+            return False
     return True
 
 
