@@ -399,6 +399,9 @@ extern "C" int spamm_create(spamm_ctx** out, int device, void* cuda_stream) {
     spamm_ctx* c = new spamm_ctx();
     memset(c, 0, sizeof(*c));
     c->device = device;
+    c->hint_tau = -1;              // no previous selection yet
+    c->hint_lmax = 0;
+    c->bound = SPAMM_BOUND_ALG3;
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
         c->own_stream = false;
