@@ -47,3 +47,25 @@ def test_strerror_without_gpu():
     lib = sp.load_library()
     assert lib.spamm_strerror(0) == b"ok"
     assert lib.spamm_strerror(1) == b"invalid argument"
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built CUDA library the binding raises
+    from paper_2005_10680_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "library_path", lambda: str(tmp_path / "missing.so"))
+    import pytest
+    with pytest.raises(ImportError):
+        _lib.load_library(build_if_stale=False)
+
+
+def test_context_without_gpu_raises():
+    # on a machine without a GPU, creating a context is an error, not a fallback
+    import pytest
+    import torch
+
+    import paper_2005_10680_gb300 as sp
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(sp.SpammError):
+        sp.Context(0)
