@@ -144,3 +144,21 @@ def test_eleventh_level_when_ten_cannot_certify(gctx, orc):
     c10 = C10.to_numpy()
     out_round = 2.3e-16 * np.linalg.norm(c10)
     assert np.linalg.norm(C.to_numpy() - c10) <= rep["bound"] + r10["bound"] + 2 * out_round
+
+
+@pytest.mark.parametrize("n", [50, 100, 130])
+def test_mixed_small_and_ragged_grids(gctx, n):
+    # one, two and three leaf blocks per side (the last one ragged): pair and tile
+    # halves beyond the grid are empty
+    g = synth.rng(n)
+    A = g.integers(-50, 51, size=(n, n)).astype(np.float64)
+    B = g.integers(-50, 51, size=(n, n)).astype(np.float64)
+    C, rep = gctx.multiply_tau(gctx.from_dense(A, 64), gctx.from_dense(B, 64), 0.0, prec="mixed")
+    np.testing.assert_array_equal(C.to_numpy(), A @ B)
+    X = synth.banded_decay(n, n, length=n / 6.0)
+    Y, yrep = gctx.sp2_step(gctx.from_dense(X, 64), 1, delta=1e-9, prec="mixed")
+    y = Y.to_numpy()
+    np.testing.assert_array_equal(y, y.T)
+    noise = 1.12e-16 * np.linalg.norm(X) ** 2 * np.sqrt(n)
+    assert np.linalg.norm(y - (2 * X - X @ X)) <= yrep["bound"] + noise
+    assert yrep["bound"] < 1e-9
