@@ -162,3 +162,16 @@ def test_mixed_small_and_ragged_grids(gctx, n):
     noise = 1.12e-16 * np.linalg.norm(X) ** 2 * np.sqrt(n)
     assert np.linalg.norm(y - (2 * X - X @ X)) <= yrep["bound"] + noise
     assert yrep["bound"] < 1e-9
+
+
+def test_mixed_zero_and_everything_skipped(gctx):
+    n = 200
+    Z = gctx.from_dense(np.zeros((n, n)), 64)
+    C, rep = gctx.multiply(Z, Z, 1e-8, prec="mixed")
+    assert rep["nnzb_out"] == 0 and rep["bound"] == 0.0 and not C.to_numpy().any()
+    X = synth.banded_decay(n, 11, length=10.0)
+    G = gctx.from_dense(X, 64)
+    # tau above every norm product: nothing is formed; the 2X - X^2 branch keeps 2X
+    C, rep = gctx.sp2_step(G, 1, tau=1e6, prec="mixed")
+    assert rep["formed"] == 0
+    np.testing.assert_array_equal(C.to_numpy(), 2 * X)
