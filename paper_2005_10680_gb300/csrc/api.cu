@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "search.h"
 
 
 using namespace spamm;
@@ -103,49 +104,31 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
             lmax_used = 10;
             err_charge = ec;
         } else {
-            int lo = 4, hi = MIXED_LMAX;
-            double ec_hi = -1.0;
-            // start from the previous step's level count and its neighbour below;
-            // the charge is non-increasing in L, so the bisection that follows
-            // returns the same L as without this start
+            // the fewest levels L in [4, MIXED_LMAX) whose charge is at most delta/2,
+            // searched from the previous step's count (the charge is non-increasing
+            // in L, so any start gives the same L); else MIXED_LMAX, where the charge
+            // may take up to 0.9 delta
+            constexpr int L0 = 4;
             const int hl = ctx->hint_lmax;
-            if (hl >= lo && hl < hi) {
-                double ec = 0.0;
-                st = charge_at(hl, &ec);
-                if (st == SPAMM_OK && ec <= 0.5 * delta) {
-                    hi = hl;
-                    ec_hi = ec;
-                    if (hl - 1 >= lo) {
-                        st = charge_at(hl - 1, &ec);
-                        if (st == SPAMM_OK && ec <= 0.5 * delta) {
-                            hi = hl - 1;
-                            ec_hi = ec;
-                        } else if (st == SPAMM_OK) {
-                            lo = hl;
-                        }
-                    }
-                } else if (st == SPAMM_OK) {
-                    lo = hl + 1;
-                }
-            }
-            while (lo < hi && st == SPAMM_OK) {
-                const int mid = (lo + hi) / 2;
-                double ec = 0.0;
-                st = charge_at(mid, &ec);
-                if (st != SPAMM_OK) break;
-                if (ec <= 0.5 * delta) {
-                    hi = mid;
-                    ec_hi = ec;
-                } else {
-                    lo = mid + 1;
-                }
-            }
+            const int hint = (hl >= L0 && hl < MIXED_LMAX) ? hl - L0
+                             : hl >= MIXED_LMAX           ? MIXED_LMAX - 1 - L0
+                                                          : (MIXED_LMAX - L0) / 2;
+            int idx = MIXED_LMAX - L0, ev = 0;
+            double ec = -1.0;
+            st = hinted_first_true(
+                MIXED_LMAX - L0, hint,
+                [&](int k, bool* fits, double* e) -> int {
+                    const int r = charge_at(L0 + k, e);
+                    *fits = *e <= 0.5 * delta;
+                    return r;
+                },
+                &idx, &ec, &ev);
             if (st == SPAMM_OK) {
-                double ec = ec_hi;
-                if (ec < 0.0) st = charge_at(lo, &ec);   // lo == MIXED_LMAX was never evaluated
+                const int L = L0 + idx;
+                if (L == MIXED_LMAX) st = charge_at(L, &ec);
                 if (st == SPAMM_OK &&
-                    (ec <= 0.5 * delta || (lo == MIXED_LMAX && ec <= 0.9 * delta))) {
-                    lmax_used = lo;
+                    (ec <= 0.5 * delta || (L == MIXED_LMAX && ec <= 0.9 * delta))) {
+                    lmax_used = L;
                     err_charge = ec;
                 }
             }

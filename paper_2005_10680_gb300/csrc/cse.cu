@@ -20,6 +20,7 @@
 // fold is monotone under round-to-nearest), so ceil(log2(N+1)) = 9 evaluations
 // replace the paper's 350-entry sweep and select the same candidate.
 #include "common.cuh"
+#include "search.h"
 
 namespace spamm {
 
@@ -304,7 +305,6 @@ int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const doubl
     SP_TRY(dalloc((void**)&b1, sizeof(double) * e, s));
     const int N = SPAMM_N_TAU;
     if (hint >= 0 && hint < N) {
-        int n_ev = 0;
         int st = SPAMM_OK;
         auto E = [&](int k, double* out) -> int {
             ++ctx->launches;
@@ -316,52 +316,18 @@ int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const doubl
                     cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess)
                 return SPAMM_ECUDA;
-            ++n_ev;
             return SPAMM_OK;
         };
-        int lo = 0, hi = N;     // the answer lies in [lo, hi]; E[hi] < delta unless hi == N
-        double ehi = 0.0, ex = 0.0;
-        st = E(hint, &ex);
-        if (st == SPAMM_OK && ex < delta) {
-            hi = hint;
-            ehi = ex;
-            for (int step = 1; hi > lo && st == SPAMM_OK; step *= 2) {
-                const int x = hi - step > lo ? hi - step : lo;
-                st = E(x, &ex);
-                if (st != SPAMM_OK) break;
-                if (ex < delta) {
-                    hi = x;
-                    ehi = ex;
-                } else {
-                    lo = x + 1;
-                    break;
-                }
-            }
-        } else if (st == SPAMM_OK) {
-            lo = hint + 1;
-            for (int step = 1; lo < hi && st == SPAMM_OK; step *= 2) {
-                const int x = lo + step - 1 < hi - 1 ? lo + step - 1 : hi - 1;
-                st = E(x, &ex);
-                if (st != SPAMM_OK) break;
-                if (ex < delta) {
-                    hi = x;
-                    ehi = ex;
-                    break;
-                }
-                lo = x + 1;
-            }
-        }
-        while (lo < hi && st == SPAMM_OK) {
-            const int mid = (lo + hi) / 2;
-            st = E(mid, &ex);
-            if (st != SPAMM_OK) break;
-            if (ex < delta) {
-                hi = mid;
-                ehi = ex;
-            } else {
-                lo = mid + 1;
-            }
-        }
+        int hi = N, ev = 0;
+        double ehi = 0.0;
+        st = hinted_first_true(
+            N, hint,
+            [&](int k, bool* below, double* e) -> int {
+                const int r = E(k, e);
+                *below = *e < delta;
+                return r;
+            },
+            &hi, &ehi, &ev);
         if (st == SPAMM_OK) {
             ++ctx->launches;
             k_set_search<<<1, 1, 0, s>>>(sc, hi, ehi);
@@ -369,7 +335,7 @@ int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const doubl
         }
         dfree(b0, s);
         dfree(b1, s);
-        if (evals) *evals = n_ev;
+        if (evals) *evals = ev;
         return st;
     }
     int steps = 0;
