@@ -13,6 +13,9 @@ What lives where:
 * this file -- ctypes wrappers, block truncation with ||E||_F < delta (the
   unit rule below), and the SP2 purification driver in the three variants of
   Algorithms 1, 4 and 5.
+* ``mixed_ref.py`` -- the mixed form's arithmetic written out exactly: the
+  fixed-point rounding, the balanced base-128 digits, level products summed in
+  Python integers, and the charge that bounds a product formed to level L.
 
 Readings where the paper is silent (each one is a choice, not the paper's):
 
