@@ -117,6 +117,22 @@ class Sliced:
         unit = self._scale(S, rows, cols)
         return (R.astype(np.float64) + self.r[rows, cols]) * unit
 
+    def tail_bound_norms(self, rows=slice(None), cols=slice(None)) -> np.ndarray:
+        """Upper bounds of tn[p] (p = 0..9): sqrt(sum (|R_p| + h)^2) in units of
+        2^(e - 63), with R_p the integer residue after digit p and h = 1/2 where the
+        rounding to fixed point was inexact, 0 where it was exact; >= ||T_p||_F since
+        |R_p + r| <= |R_p| + |r| and |r| <= h."""
+        dw = self.d[:, rows, cols]
+        h = np.where(self.r[rows, cols] != 0.0, 0.5, 0.0)
+        unit = self._scale(S, rows, cols)
+        out = []
+        for p in range(0, S + 1):
+            R = np.zeros(dw.shape[1:], dtype=np.int64)
+            for q in range(p + 1, S + 1):
+                R = R + dw[q - 1] * (np.int64(1) << (W * (S - q)))
+            out.append(np.linalg.norm((np.abs(R).astype(np.float64) + h) * unit))
+        return np.array(out)
+
     def slice_norms(self, rows=slice(None), cols=slice(None)) -> np.ndarray:
         """sn[p - 1] = ||X_p||_F on a window, p = 1..9."""
         return np.array([np.linalg.norm(self.part(p, rows, cols)) for p in range(1, S + 1)])
@@ -162,6 +178,31 @@ def charge(snA: np.ndarray, tnA: np.ndarray, tnB: np.ndarray, norm_b: float, L: 
     for p in range(1, m + 1):
         c += snA[p - 1] * tnB[min(L - p, S)]
     return float(c)
+
+
+def triple_charges(A: np.ndarray, B: np.ndarray, bs: int, levels, bound_tails: bool = False):
+    """charge(L) of every leaf triple (i, k, j) of A B on bs x bs blocks, slices cut with
+    whole-row (A) and whole-column (B) exponents: {L: array[nb, nb, nb]} indexed
+    [i, k, j]. bound_tails: use the tail upper bounds instead of the exact tails."""
+    n = A.shape[0]
+    nb = -(-n // bs)
+    SA, SB = Sliced(A, True), Sliced(B, False)
+    win = [slice(x * bs, min((x + 1) * bs, n)) for x in range(nb)]
+    tail = (lambda Sx, r, c: Sx.tail_bound_norms(r, c)) if bound_tails else \
+           (lambda Sx, r, c: Sx.tail_norms(r, c))
+    snA = {(i, k): SA.slice_norms(win[i], win[k]) for i in range(nb) for k in range(nb)}
+    tnA = {(i, k): tail(SA, win[i], win[k]) for i in range(nb) for k in range(nb)}
+    tnB = {(k, j): tail(SB, win[k], win[j]) for k in range(nb) for j in range(nb)}
+    nB = {(k, j): float(np.linalg.norm(B[win[k], win[j]])) for k in range(nb) for j in range(nb)}
+    out = {}
+    for L in levels:
+        c = np.zeros((nb, nb, nb))
+        for i in range(nb):
+            for k in range(nb):
+                for j in range(nb):
+                    c[i, k, j] = charge(snA[i, k], tnA[i, k], tnB[k, j], nB[k, j], L)
+        out[L] = c
+    return out
 
 
 def to_int(X: np.ndarray):

@@ -247,3 +247,33 @@ def test_mutated_charges_fail(mutant, kind):
     A, B = _case(kind, rng)
     violated = [(L, err, c) for err, c, L in _charged_errors(A, B, mutant) if err > c * (1 + 1e-12)]
     assert violated, mutant.__name__
+
+
+# ------------------------------------------------ inputs of the GPU level check
+
+def test_alg3_recursion_matches_the_oracle(orc):
+    """The recursion tests/levels_case.py applies to leaf charges is Algorithm 3: on
+    float64 leaves (p if p < tau, else 0) it reproduces the oracle's CSE."""
+    import levels_case
+    g = np.random.default_rng(3)
+    n = 256
+    A = g.standard_normal((n, n)) * np.exp(-np.abs(np.subtract.outer(np.arange(n), np.arange(n))) / 40)
+    B = A.T.copy()
+    nA, nB = orc.block_norms(A, 64), orc.block_norms(B, 64)
+    p = nA[:, :, None] * nB[None, :, :]
+    taus = np.array([0.0, np.median(p), p.max() * 1.01, 1e9])
+    want = orc.cse(A, B, 64, taus)
+    for t, w in zip(taus, want):
+        leaf = np.where(p < t, p, 0.0)
+        assert levels_case.alg3(leaf) == pytest.approx(w, rel=1e-12, abs=0.0)
+
+
+@pytest.mark.parametrize("case", __import__("levels_case").CASES)
+def test_level_cases_separate_levels(case):
+    """Each GPU level case fixes exactly one level (checked inside build), and the
+    results one level up or down differ from the expected one by far more than the
+    rounding tolerance, so a level set off by one cannot pass."""
+    import levels_case
+    c = levels_case.build(*case)
+    assert c.charge_lo <= c.charge_hi <= c.delta / 2
+    assert c.neighbours.min() > 0.9, c.neighbours
