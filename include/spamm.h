@@ -124,7 +124,8 @@ int spamm_set_bound(spamm_ctx* ctx, spamm_bound bound);
 /* Build a block-sparse matrix from a dense n x n row-major array (leading
    dimension ld >= n), host or device memory as `a_on_device` says. Entries
    with |x| < drop_abs become zero; a leaf block whose entries are all zero is
-   not stored. bs must be 32, 64 or 128. */
+   not stored. bs must be 32, 64 or 128. SPAMM_EINVAL when an entry is NaN or
+   infinite, or a leaf norm overflows float64 (the bounds compare norms). */
 int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, int64_t ld, int bs,
                          double drop_abs, int a_on_device, spamm_mat** out);
 
@@ -134,7 +135,9 @@ int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, int64_t ld,
    arrays), its bs x bs entries row-major at tiles + t * bs * bs (host or device
    memory as `tiles_on_device` says; copied). Entries of a block that fall outside
    the n x n matrix are set to zero. Blocks not listed are zero. bs must be 32, 64
-   or 128. SPAMM_EINVAL for a bad index, a repeated block or a bad size. */
+   or 128. SPAMM_EINVAL for a bad index, a repeated block or a bad size, and, as
+   for spamm_mat_from_dense, for entries inside the matrix that are NaN or
+   infinite or whose leaf norm overflows float64. */
 int spamm_mat_from_blocks(spamm_ctx* ctx, int64_t n, int bs, int64_t nnzb, const int32_t* brow,
                           const int32_t* bcol, const double* tiles, int tiles_on_device,
                           spamm_mat** out);

@@ -189,7 +189,8 @@ __global__ void k_block_present(const double* __restrict__ a, int64_t n, int64_t
         int64_t r = (int64_t)bi * bs + e / bs, c = (int64_t)bj * bs + e % bs;
         if (r < n && c < n) {
             double x = a[r * ld + c];
-            if (x != 0.0 && fabs(x) >= drop) any = 1;
+            // NaN counts as present, so that the finiteness check below sees it
+            if (x != 0.0 && !(fabs(x) < drop)) any = 1;
         }
     }
     any = __syncthreads_or(any);
@@ -240,6 +241,42 @@ __global__ void k_tile_norms(const double* __restrict__ tiles, const int32_t* __
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) norm[c] = sqrt(s);
+}
+
+// *bad = 1 when a block norm is not finite: an entry is NaN or infinite, or the
+// squares of finite entries overflow float64. Norms of absent blocks are 0.
+__global__ void k_norms_finite(const double* __restrict__ norm, int64_t count,
+                               int* __restrict__ bad) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(norm[i])) *bad = 1;
+}
+
+// Constructors reject matrices whose norms are not finite: the bounds of Algorithm 3
+// and the truncation rule compare norms, and NaN compares false everywhere.
+static int mat_check_finite(spamm_ctx* ctx, const spamm_mat* m, const char* who) {
+    cudaStream_t s = ctx->stream;
+    const int64_t count = (int64_t)m->nb * m->nb;
+    int* d_bad = nullptr;
+    SP_TRY(dalloc((void**)&d_bad, sizeof(int), s));
+    int bad = 0;
+    cudaError_t e = cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+        const int64_t want = (count + 255) / 256;
+        const unsigned blocks = (unsigned)(want < 4096 ? (want > 0 ? want : 1) : 4096);
+        ++ctx->launches;
+        k_norms_finite<<<blocks, 256, 0, s>>>(m->d_norm, count, d_bad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    dfree(d_bad, s);
+    if (e != cudaSuccess) return cuda_fail(e, who, __FILE__, __LINE__);
+    if (bad) {
+        set_error("%s: entries that are NaN or infinite, or too large for float64 norms", who);
+        return SPAMM_EINVAL;
+    }
+    return SPAMM_OK;
 }
 
 int mat_compute_norms(spamm_ctx* ctx, spamm_mat* m) {
@@ -392,6 +429,7 @@ extern "C" int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, 
                                       m->d_coord, m->d_tiles);
     SP_CHECK_LAUNCH();
     int st = mat_compute_norms(ctx, m);
+    if (st == SPAMM_OK) st = mat_check_finite(ctx, m, "spamm_mat_from_dense");
     dfree(present, s);
     dfree(slot, s);
     dfree(d_tot, s);
@@ -477,6 +515,7 @@ extern "C" int spamm_mat_from_blocks(spamm_ctx* ctx, int64_t n, int bs, int64_t 
         }
     }
     if (st == SPAMM_OK) st = mat_compute_norms(ctx, m);
+    if (st == SPAMM_OK) st = mat_check_finite(ctx, m, "spamm_mat_from_blocks");
     if (st == SPAMM_OK && cudaStreamSynchronize(s) != cudaSuccess) st = SPAMM_ECUDA;
     if (st != SPAMM_OK) {
         if (st == SPAMM_ECUDA) set_error("spamm_mat_from_blocks: CUDA error");

@@ -285,3 +285,29 @@ def test_from_blocks_rejects_bad_lists(gctx):
         gctx.from_blocks(64, 32, [0, 2], [0, 0], t)       # outside the 2 x 2 block grid
     E = gctx.from_blocks(64, 32, [], [], np.zeros((0, 32, 32)))
     assert E.nnzb == 0 and not E.to_numpy().any()
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf, 1e300])
+def test_constructors_reject_non_finite_entries(gctx, bad):
+    """NaN or infinite entries, or entries whose squares overflow, make the leaf norms
+    that Algorithm 3 and the truncation compare meaningless: both constructors
+    refuse them with SPAMM_EINVAL, including in a block that holds nothing else."""
+    import paper_2005_10680_gb300 as sp
+    A = np.zeros((100, 100))
+    A[3, 5] = 1.0
+    A[70, 90] = bad                      # block (1, 1) holds only this entry
+    for drop in (0.0, 1e-3):
+        with pytest.raises(sp.SpammError) as ei:
+            gctx.from_dense(A, 64, drop=drop)
+        assert ei.value.status == 1
+    t = np.zeros((2, 64, 64))
+    t[0, 0, 0] = 2.0
+    t[1, 6, 26] = bad                    # entry (70, 90) of block (1, 1)
+    with pytest.raises(sp.SpammError) as ei:
+        gctx.from_blocks(100, 64, [0, 1], [0, 1], t)
+    assert ei.value.status == 1
+    # outside the matrix (n = 100) the entry is zeroed before the norms: accepted
+    t[1, 6, 26] = 0.0
+    t[1, 50, 50] = bad
+    M = gctx.from_blocks(100, 64, [0, 1], [0, 1], t)
+    assert np.isfinite(M.to_numpy()).all()
