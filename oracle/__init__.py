@@ -80,6 +80,10 @@ def lib():
         _lib.or_spamm.restype = i64
         _lib.or_cse.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
         _lib.or_flat_bound.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
+        _lib.or_tau_table_scaled.argtypes = [i32, d, d, pd]
+        _lib.or_spectral_norm_bound.argtypes = [i64, pd]
+        _lib.or_spectral_norm_bound.restype = d
+        _lib.or_spectral_bound.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
         _lib.or_select_tau.argtypes = [pd, i32, d]
         _lib.or_select_tau.restype = i32
         _lib.or_dense_gemm.argtypes = [i64, pd, pd, pd]
@@ -130,6 +134,31 @@ def flat_bound(A, B, bs: int, taus=None) -> np.ndarray:
     n = A.shape[0]
     err = np.zeros(len(taus))
     lib().or_flat_bound(n, bs, _p(A), n, _p(B), n, _p(taus), len(taus), _p(err))
+    return err
+
+
+def tau_table_scaled(N: int, start: float, ratio: float) -> np.ndarray:
+    """tau_1 = start, tau_i = ratio tau_{i-1} (repeated multiplication)."""
+    out = np.zeros(N)
+    lib().or_tau_table_scaled(N, float(start), float(ratio), _p(out))
+    return out
+
+
+def spectral_norm_bound(M) -> float:
+    """min(||M||_F, sqrt(||M||_1 ||M||_inf)) for a square M: an upper bound on ||M||_2."""
+    M = _f64(M)
+    assert M.ndim == 2 and M.shape[0] == M.shape[1]
+    return float(lib().or_spectral_norm_bound(M.shape[0], _p(M)))
+
+
+def spectral_bound(A, B, bs: int, taus=None) -> np.ndarray:
+    """Bound on ||SpAMM(A, B, tau) - AB||_2 for every tau: spectral_norm_bound of
+    M_ij = sum_k p_ikj [p_ikj < tau]."""
+    A, B = _f64(A), _f64(B)
+    taus = tau_table() if taus is None else _f64(taus)
+    n = A.shape[0]
+    err = np.zeros(len(taus))
+    lib().or_spectral_bound(n, bs, _p(A), n, _p(B), n, _p(taus), len(taus), _p(err))
     return err
 
 

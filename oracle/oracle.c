@@ -23,6 +23,12 @@
  *   or_flat_bound  -- the one-level bound sqrt(sum_ij (sum_k p_ikj [p_ikj < tau])^2)
  *                     over leaf norm products (the sharper bound the paper's
  *                     discussion of future work points to), one entry per tau.
+ *   or_tau_table_scaled -- the candidate list with a chosen start and ratio
+ *                     (the conclusion's "length and starting value").
+ *   or_spectral_norm_bound, or_spectral_bound -- error control in the spectral
+ *                     norm (the conclusion's "other norms"): ||E||_2 <= ||M||_2
+ *                     with M_ij = sum_k p_ikj [p_ikj < tau], bounded by
+ *                     min(||M||_F, sqrt(||M||_1 ||M||_inf)).
  *
  * Quadrant indexing: Algorithm 2 uses C_ij = A_i0 B_0j + A_i1 B_1j with the
  * first index the row half, so child[r][c] below is (row half r, column
@@ -299,4 +305,81 @@ void or_flat_bound(int64_t n, int64_t bs, const double* A, int64_t lda, const do
     }
     free(na);
     free(nbn);
+}
+
+/* ---------------------------------------------- tuned tau list (conclusion) */
+
+/*
+ * The candidate list with its starting value and ratio chosen by the caller:
+ * tau_1 = start, tau_i = ratio * tau_{i-1} by repeated float64 multiplication.
+ * The paper's conclusion names the list's length and starting value as the
+ * knobs that cut the cost of the selection; start = 1, ratio = 0.9 is
+ * or_tau_table.
+ */
+void or_tau_table_scaled(int N, double start, double ratio, double* tau) {
+    if (N <= 0) return;
+    tau[0] = start;
+    for (int i = 1; i < N; ++i) tau[i] = ratio * tau[i - 1];
+}
+
+/* ------------------------------------------- spectral-norm error control */
+
+/*
+ * Upper bound on ||M||_2 for an nb x nb matrix M (row-major, non-negative here):
+ * min(||M||_F, sqrt(||M||_1 ||M||_inf)), the Frobenius norm or the Schur test with
+ * unit weights, ||M||_1 the largest column sum and ||M||_inf the largest row sum.
+ * Both are non-decreasing in every entry of a non-negative M.
+ */
+double or_spectral_norm_bound(int64_t nb, const double* M) {
+    double fro2 = 0.0, rmax = 0.0, cmax = 0.0;
+    for (int64_t i = 0; i < nb; ++i) {
+        double r = 0.0;
+        for (int64_t j = 0; j < nb; ++j) {
+            r += M[i * nb + j];
+            fro2 += M[i * nb + j] * M[i * nb + j];
+        }
+        if (r > rmax) rmax = r;
+    }
+    for (int64_t j = 0; j < nb; ++j) {
+        double c = 0.0;
+        for (int64_t i = 0; i < nb; ++i) c += M[i * nb + j];
+        if (c > cmax) cmax = c;
+    }
+    double fro = sqrt(fro2), sch = sqrt(rmax * cmax);
+    return sch < fro ? sch : fro;
+}
+
+/*
+ * Error control in the spectral norm over the leaf products of or_flat_bound
+ * (the conclusion leaves control in other norms to future work):
+ *   M_ij(tau) = sum_k s_ikj,  s_ikj = ||A_ik||_F ||B_kj||_F if below tau, else 0.
+ * E = SpAMM(A, B, tau) - A B has blocks E_ij = -(sum of the skipped A_ik B_kj), so
+ * ||E_ij||_2 <= ||E_ij||_F <= M_ij; a block matrix has ||E||_2 at most the spectral
+ * norm of its matrix of block norms, and the spectral norm is monotone on
+ * non-negative matrices: ||E||_2 <= ||M(tau)||_2 <= or_spectral_norm_bound(M(tau)),
+ * non-increasing along the table like Algorithm 3's bound.
+ */
+void or_spectral_bound(int64_t n, int64_t bs, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, const double* tau, int N, double* errors) {
+    int64_t nb = (n + bs - 1) / bs;
+    double* na = (double*)malloc(sizeof(double) * nb * nb);
+    double* nbn = (double*)malloc(sizeof(double) * nb * nb);
+    double* M = (double*)malloc(sizeof(double) * nb * nb);
+    or_block_norms(n, bs, A, lda, na);
+    or_block_norms(n, bs, B, ldb, nbn);
+    for (int t = 0; t < N; ++t) {
+        for (int64_t i = 0; i < nb; ++i)
+            for (int64_t j = 0; j < nb; ++j) {
+                double sum = 0.0;
+                for (int64_t k = 0; k < nb; ++k) {
+                    double pk = na[i * nb + k] * nbn[k * nb + j];
+                    if (pk < tau[t]) sum += pk;
+                }
+                M[i * nb + j] = sum;
+            }
+        errors[t] = or_spectral_norm_bound(nb, M);
+    }
+    free(na);
+    free(nbn);
+    free(M);
 }

@@ -31,6 +31,16 @@ MUTANTS = {
     "flat_no_sqrt": ("errors[t] = sqrt(total);", "errors[t] = total;"),
     "flat_transposed_b": ("double p = na[i * nb + k] * nbn[k * nb + j];",
                           "double p = na[i * nb + k] * nbn[j * nb + k];"),
+    "spectral_rows_only": ("double fro = sqrt(fro2), sch = sqrt(rmax * cmax);",
+                           "double fro = sqrt(fro2), sch = sqrt(rmax * rmax);"),
+    "spectral_no_sqrt": ("double fro = sqrt(fro2), sch = sqrt(rmax * cmax);",
+                         "double fro = sqrt(fro2), sch = rmax * cmax;"),
+    "spectral_max_not_min": ("return sch < fro ? sch : fro;", "return sch < fro ? fro : sch;"),
+    "spectral_non_strict": ("if (pk < tau[t]) sum += pk;", "if (pk <= tau[t]) sum += pk;"),
+    "spectral_transposed_b": ("double pk = na[i * nb + k] * nbn[k * nb + j];",
+                              "double pk = na[i * nb + k] * nbn[j * nb + k];"),
+    "tau_scaled_fixed_ratio": ("for (int i = 1; i < N; ++i) tau[i] = ratio * tau[i - 1];",
+                               "for (int i = 1; i < N; ++i) tau[i] = 0.9 * tau[i - 1];"),
 }
 
 
@@ -49,6 +59,10 @@ def _build(tmp_path, name, old, new):
     lib.or_spamm.restype = i64
     lib.or_cse.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
     lib.or_flat_bound.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
+    lib.or_tau_table_scaled.argtypes = [i32, d, d, pd]
+    lib.or_spectral_norm_bound.argtypes = [i64, pd]
+    lib.or_spectral_norm_bound.restype = d
+    lib.or_spectral_bound.argtypes = [i64, i64, pd, i64, pd, i64, pd, i32, pd]
     return lib
 
 
@@ -81,6 +95,33 @@ def _pins_hold(lib) -> bool:
         lib.or_flat_bound(A.shape[0], bs, _p(A), A.shape[0], _p(B), A.shape[0], _p(taus), len(taus), _p(e))
         return e
 
+    def spectral(A, B, bs, taus):
+        A, B, taus = np.ascontiguousarray(A), np.ascontiguousarray(B), np.ascontiguousarray(taus, dtype=float)
+        e = np.zeros(len(taus))
+        lib.or_spectral_bound(A.shape[0], bs, _p(A), A.shape[0], _p(B), A.shape[0], _p(taus), len(taus), _p(e))
+        return e
+
+    def snb(M):
+        M = np.ascontiguousarray(M, dtype=float)
+        return lib.or_spectral_norm_bound(M.shape[0], _p(M))
+
+    ts = np.zeros(6)
+    lib.or_tau_table_scaled(6, 64.0, 0.97, _p(ts))
+    if not np.allclose(ts, 64.0 * 0.97 ** np.arange(6), rtol=1e-14, atol=0):
+        return False
+    # spectral norm bound: closed forms (a column of ones, a permutation, a diagonal)
+    col = np.zeros((8, 8))
+    col[:, 0] = 1.0
+    if abs(snb(col) - np.sqrt(8.0)) > 1e-14 or abs(snb(np.eye(8)[::-1]) - 1.0) > 1e-15:
+        return False
+    if abs(snb(np.diag([3.0, 1.0, 2.0])) - 3.0) > 1e-15 or snb(np.zeros((3, 3))) != 0.0:
+        return False
+    # a column of ones as the skipped product: ||E||_2 = sqrt(8)
+    if abs(spectral(col, np.eye(8), 1, [2.0])[0] - np.sqrt(8.0)) > 1e-14:
+        return False
+    J8 = np.ones((8, 8))
+    if spectral(J8, J8, 1, [1.0])[0] != 0.0:      # products equal to tau are kept
+        return False
     A = np.array([[1.0, 2.0], [3.0, 4.0]])
     B = np.array([[5.0, 6.0], [7.0, 8.0]])
     if not np.array_equal(spamm(A, B, 15.5, 1), np.array([[0.0, 16.0], [28.0, 50.0]])):
@@ -118,6 +159,13 @@ def _pins_hold(lib) -> bool:
                 return False
         if np.any(f > b * (1 + 1e-13)):
             return False
+        sp = spectral(X, Y, 8, tau)
+        if np.any(sp > f * (1 + 1e-13)) or np.any(np.diff(sp) > 0):
+            return False
+        for k in range(0, 350, 25):
+            err2 = np.linalg.norm(X @ Y - spamm(X, Y, tau[k], 8), 2)
+            if err2 > sp[k] * (1 + 1e-12) + 1e-13:
+                return False
     return True
 
 
