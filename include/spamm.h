@@ -56,8 +56,16 @@ typedef enum { SPAMM_FP64 = 0, SPAMM_MIXED = 1 } spamm_prec;
    still an upper bound on ||E||_F (triangle inequality per block) and never
    exceeds Algorithm 3's (Minkowski's inequality), so it certifies at least as
    large a tau. The paper's discussion of future work names it as a sharper
-   bound; it has no counterpart among the paper's algorithms. */
-typedef enum { SPAMM_BOUND_ALG3 = 0, SPAMM_BOUND_FLAT = 1 } spamm_bound;
+   bound; it has no counterpart among the paper's algorithms.
+   SPECTRAL: error control in the spectral norm, which the conclusion leaves to
+   future work: with M_ij = sum_k e_ikj over the same leaf terms, the bound is
+   min(||M||_F, sqrt(||M||_1 ||M||_inf)) >= ||M||_2 >= ||E||_2 (a block matrix's
+   spectral norm is at most that of its matrix of block norms, each block norm is
+   at most M_ij, and the spectral norm is monotone on non-negative matrices). A
+   delta passed to spamm_multiply or spamm_sp2_step then certifies ||E||_2 < delta,
+   and every reported bound is in the spectral norm. Never above FLAT. The
+   purification drivers keep a Frobenius guarantee and refuse it (SPAMM_EINVAL). */
+typedef enum { SPAMM_BOUND_ALG3 = 0, SPAMM_BOUND_FLAT = 1, SPAMM_BOUND_SPECTRAL = 2 } spamm_bound;
 
 /* Purification variants, numbered as the paper's algorithms:
    1 = multiply exactly then truncate (Algorithm 1, "truncmul"),
@@ -118,6 +126,16 @@ int spamm_prec_supported(const spamm_ctx* ctx, spamm_prec prec, int bs);
    spamm_multiply, spamm_sp2_step, spamm_purify). SPAMM_EINVAL for an unknown
    value. */
 int spamm_set_bound(spamm_ctx* ctx, spamm_bound bound);
+
+/* Replace the context's tau candidates by tau_1 = start, tau_i = ratio tau_{i-1}
+   (i = 2..SPAMM_N_TAU, repeated float64 multiplication): the list's starting value
+   and spacing, which the conclusion names as ways to cut the cost of the selection
+   or to bring the certified bound closer to delta. start = 1, ratio = 0.9 is the
+   paper's list (the default). Applies to later searches on ctx (spamm_multiply,
+   spamm_sp2_step, spamm_purify, spamm_purify_batched); the allocation-free search
+   keeps the paper's list. SPAMM_EINVAL unless start is finite and > 0, 0 < ratio < 1
+   and the last candidate is a normal float64. */
+int spamm_set_tau_table(spamm_ctx* ctx, double start, double ratio);
 
 /* --------------------------------------------------------------- matrices */
 

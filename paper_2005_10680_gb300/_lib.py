@@ -111,6 +111,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_cse_search_noalloc": ([vp, vp, i64, d, vp, vp, vp, vp], i32),
         "spamm_autotune": ([vp, vp, d, i32, P(TuneResult)], i32),
         "spamm_set_bound": ([vp, i32], i32),
+        "spamm_set_tau_table": ([vp, d, d], i32),
         "spamm_purify_batched": ([vp, i32, P(vp), P(i64), d, i32, P(PurifyOpts), i32, P(vp),
                                   P(PurifyReport), P(ctypes.c_int32)], i32),
     }
@@ -382,8 +383,15 @@ class Context:
                        "mixed_bs64": r.ms[3]}, "cached": bool(r.cached)}
 
     def set_bound(self, bound: str = "alg3"):
-        """Bound for later searches on this context: "alg3" (Algorithm 3) or "flat"."""
-        _check(_lib.spamm_set_bound(self.handle, {"alg3": 0, "flat": 1}[bound]), "spamm_set_bound")
+        """Bound for later searches on this context: "alg3" (Algorithm 3), "flat" (one
+        level) or "spectral" (certifies the spectral norm of the error)."""
+        _check(_lib.spamm_set_bound(self.handle, {"alg3": 0, "flat": 1, "spectral": 2}[bound]),
+               "spamm_set_bound")
+
+    def set_tau_table(self, start: float = 1.0, ratio: float = 0.9):
+        """tau candidates tau_1 = start, tau_i = ratio tau_{i-1} for later searches."""
+        _check(_lib.spamm_set_tau_table(self.handle, float(start), float(ratio)),
+               "spamm_set_tau_table")
 
     def from_blocks(self, n: int, bs: int, brow, bcol, tiles) -> Matrix:
         """Matrix from a list of leaf blocks: tiles[t] (bs x bs) at block (brow[t], bcol[t]).

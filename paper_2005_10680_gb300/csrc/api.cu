@@ -416,12 +416,44 @@ extern "C" int64_t spamm_ctx_launches(const spamm_ctx* c) {
 }
 
 extern "C" int spamm_set_bound(spamm_ctx* ctx, spamm_bound bound) {
-    if (!ctx || (bound != SPAMM_BOUND_ALG3 && bound != SPAMM_BOUND_FLAT)) {
+    if (!ctx || (bound != SPAMM_BOUND_ALG3 && bound != SPAMM_BOUND_FLAT &&
+                 bound != SPAMM_BOUND_SPECTRAL)) {
         set_error("spamm_set_bound: bad argument");
         return SPAMM_EINVAL;
     }
     ctx->bound = bound;
     return SPAMM_OK;
+}
+
+namespace spamm {
+
+// Install a host tau table (SPAMM_N_TAU entries) as ctx's candidates.
+int tau_table_install(spamm_ctx* ctx, const double* h) {
+    memcpy(ctx->h_tau, h, sizeof(double) * SPAMM_N_TAU);
+    SP_CUDA(cudaSetDevice(ctx->device));
+    SP_CUDA(cudaMemcpyAsync(ctx->d_tau, ctx->h_tau, sizeof(double) * SPAMM_N_TAU,
+                            cudaMemcpyHostToDevice, ctx->stream));
+    SP_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->hint_tau = -1;   // an index into the old list means nothing in the new one
+    return SPAMM_OK;
+}
+
+}  // namespace spamm
+
+extern "C" int spamm_set_tau_table(spamm_ctx* ctx, double start, double ratio) {
+    if (!ctx || !(start > 0.0) || !std::isfinite(start) || !(ratio > 0.0) || !(ratio < 1.0)) {
+        set_error("spamm_set_tau_table: need ctx, a finite start > 0 and 0 < ratio < 1");
+        return SPAMM_EINVAL;
+    }
+    double t[SPAMM_N_TAU];
+    t[0] = start;
+    for (int i = 1; i < SPAMM_N_TAU; ++i) t[i] = ratio * t[i - 1];
+    if (!std::isnormal(t[SPAMM_N_TAU - 1])) {
+        set_error("spamm_set_tau_table: the last candidate %g is not a normal float64",
+                  t[SPAMM_N_TAU - 1]);
+        return SPAMM_EINVAL;
+    }
+    return tau_table_install(ctx, t);
 }
 
 extern "C" int spamm_prec_supported(const spamm_ctx* c, spamm_prec prec, int bs) {
@@ -520,6 +552,12 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
         (opts->variant != SPAMM_TRUNCMUL && opts->variant != SPAMM_APPROX &&
          opts->variant != SPAMM_HYBRID)) {
         set_error("spamm_purify: bad argument (need homo < lumo, eps > 0, 0 <= n_occ <= n)");
+        return SPAMM_EINVAL;
+    }
+    if (ctx->bound == SPAMM_BOUND_SPECTRAL) {
+        // the step tolerances and the stop rule bound the subspace error through
+        // Frobenius norms of the step errors
+        set_error("spamm_purify: needs a Frobenius-norm bound (alg3 or flat), not spectral");
         return SPAMM_EINVAL;
     }
     *D = nullptr;

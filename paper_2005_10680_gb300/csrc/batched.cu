@@ -21,6 +21,10 @@ extern "C" int spamm_purify_batched(spamm_ctx* ctx, int count, const spamm_mat* 
         set_error("spamm_purify_batched: bad argument");
         return SPAMM_EINVAL;
     }
+    if (ctx->bound == SPAMM_BOUND_SPECTRAL) {
+        set_error("spamm_purify_batched: needs a Frobenius-norm bound (alg3 or flat), not spectral");
+        return SPAMM_EINVAL;
+    }
     for (int i = 0; i < count; ++i) {
         D[i] = nullptr;
         status[i] = SPAMM_EINVAL;
@@ -45,7 +49,12 @@ extern "C" int spamm_purify_batched(spamm_ctx* ctx, int count, const spamm_mat* 
                 failed.fetch_add(1);
                 return;
             }
-            wc->bound = bound;   // the caller's choice of error bound
+            wc->bound = bound;   // the caller's choice of error bound and tau candidates
+            if (tau_table_install(wc, ctx->h_tau) != SPAMM_OK) {
+                spamm_destroy(wc);
+                failed.fetch_add(1);
+                return;
+            }
             for (;;) {
                 const int i = next.fetch_add(1);
                 if (i >= count) break;

@@ -183,6 +183,7 @@ int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const doubl
                double delta, const ChargeData& ch, int* evals, int hint = -1);
 // out[i,j] = in[min(i,j), max(i,j)]: a bitwise-symmetric copy of a norm map
 int sym_norms(spamm_ctx* ctx, const double* in, int nb, double* out);
+int tau_table_install(spamm_ctx* ctx, const double* h);
 
 // planning of the kept leaf products for C = A B (and the SP2 epilogue union)
 struct Plan {

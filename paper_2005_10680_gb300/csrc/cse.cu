@@ -104,17 +104,21 @@ __device__ __forceinline__ double leaf_value(const double* __restrict__ nA,
 // Flat (one-level) bound sqrt(sum_ij (sum_k leaf_ikj)^2): by the triangle inequality
 // per block it bounds the error as Algorithm 3 does, and by Minkowski's inequality it
 // never exceeds Algorithm 3's hierarchical value. One block per row i of C: per j the
-// k-sum in a fixed tree, then rows[i] = sum_j S_ij^2 in order of j.
+// k-sum M_ij in a fixed tree, then rows[i] = sum_j M_ij^2 in order of j. For the
+// spectral bound also rsum[i] = sum_j M_ij (same order) and M itself (row-major),
+// when those pointers are given.
 __global__ void __launch_bounds__(256) k_flat_rows(const double* __restrict__ nA,
                                                    const double* __restrict__ nB, int nb,
                                                    const double* __restrict__ d_tau, ChargeData ch,
                                                    const int32_t* __restrict__ d_done,
-                                                   double* __restrict__ rows) {
+                                                   double* __restrict__ rows,
+                                                   double* __restrict__ rsum,
+                                                   double* __restrict__ M) {
     if (d_done && *d_done) return;
     __shared__ double sh[256];
     const int i = blockIdx.x, t = threadIdx.x;
     const double tau = *d_tau;
-    double row = 0.0;
+    double row = 0.0, sum = 0.0;
     for (int j = 0; j < nb; ++j) {
         double v = 0.0;
         for (int k = t; k < nb; k += 256) v += leaf_value(nA, nB, nb, ch, tau, i, k, j);
@@ -124,10 +128,62 @@ __global__ void __launch_bounds__(256) k_flat_rows(const double* __restrict__ nA
             if (t < o) sh[t] += sh[t + o];
             __syncthreads();
         }
-        if (t == 0) row = fma(sh[0], sh[0], row);
+        if (t == 0) {
+            row = fma(sh[0], sh[0], row);
+            sum += sh[0];
+            if (M) M[(int64_t)i * nb + j] = sh[0];
+        }
         __syncthreads();
     }
-    if (t == 0) rows[i] = row;
+    if (t == 0) {
+        rows[i] = row;
+        if (rsum) rsum[i] = sum;
+    }
+}
+
+// csum[j] = sum_i M_ij in order of i (one thread per column j).
+__global__ void k_col_sums(const double* __restrict__ M, int nb, const int32_t* __restrict__ d_done,
+                           double* __restrict__ csum) {
+    if (d_done && *d_done) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nb) return;
+    double c = 0.0;
+    for (int i = 0; i < nb; ++i) c += M[(int64_t)i * nb + j];
+    csum[j] = c;
+}
+
+// Spectral bound min(||M||_F, sqrt(||M||_1 ||M||_inf)) >= ||M||_2 >= ||E||_2. ||M||_F is
+// summed exactly as k_flat_total does, so the result never exceeds the flat bound.
+__global__ void __launch_bounds__(1024) k_spectral_total(const double* __restrict__ rows,
+                                                         const double* __restrict__ rsum,
+                                                         const double* __restrict__ csum, int nb,
+                                                         const int32_t* __restrict__ d_done,
+                                                         double* __restrict__ d_err) {
+    if (d_done && *d_done) return;
+    __shared__ double sh[1024], sr[1024], sc[1024];
+    const int t = threadIdx.x;
+    double v = 0.0, r = 0.0, c = 0.0;
+    for (int i = t; i < nb; i += 1024) {
+        v += rows[i];
+        r = fmax(r, rsum[i]);
+        c = fmax(c, csum[i]);
+    }
+    sh[t] = v;
+    sr[t] = r;
+    sc[t] = c;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (t < o) {
+            sh[t] += sh[t + o];
+            sr[t] = fmax(sr[t], sr[t + o]);
+            sc[t] = fmax(sc[t], sc[t + o]);
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        const double fro = sqrt(sh[0]), sch = sqrt(sr[0] * sc[0]);
+        *d_err = sch < fro ? sch : fro;
+    }
 }
 
 __global__ void __launch_bounds__(1024) k_flat_total(const double* __restrict__ rows, int nb,
@@ -186,10 +242,27 @@ int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const do
         SP_TRY(dalloc((void**)&rows, sizeof(double) * (nb > 0 ? nb : 1), s));
         ++ctx->launches;
         k_flat_rows<<<(unsigned)(nb > 0 ? nb : 1), 256, 0, s>>>(nA, nB, nb, d_tau, d_charge,
-                                                                d_done, rows);
+                                                                d_done, rows, nullptr, nullptr);
         ++ctx->launches;
         k_flat_total<<<1, 1024, 0, s>>>(rows, nb, d_done, d_err);
         SP_CHECK_LAUNCH();
+        dfree(rows, s);
+        return SPAMM_OK;
+    }
+    if (ctx->bound == SPAMM_BOUND_SPECTRAL) {
+        const int64_t m = nb > 0 ? nb : 1;
+        double *rows = nullptr, *M = nullptr;
+        SP_TRY(dalloc((void**)&rows, sizeof(double) * 3 * m, s));   // rows, rsum, csum
+        SP_TRY(dalloc((void**)&M, sizeof(double) * m * m, s));
+        ++ctx->launches;
+        k_flat_rows<<<(unsigned)m, 256, 0, s>>>(nA, nB, nb, d_tau, d_charge, d_done, rows,
+                                                rows + m, M);
+        ++ctx->launches;
+        k_col_sums<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(M, nb, d_done, rows + 2 * m);
+        ++ctx->launches;
+        k_spectral_total<<<1, 1024, 0, s>>>(rows, rows + m, rows + 2 * m, nb, d_done, d_err);
+        SP_CHECK_LAUNCH();
+        dfree(M, s);
         dfree(rows, s);
         return SPAMM_OK;
     }
