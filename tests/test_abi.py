@@ -69,3 +69,42 @@ def test_context_without_gpu_raises():
         pytest.skip("a GPU is present")
     with pytest.raises(sp.SpammError):
         sp.Context(0)
+
+
+def test_entry_points_reject_null_handles_without_a_gpu():
+    """Every entry point checks its handles before any CUDA call: null handles give
+    SPAMM_EINVAL (1) with a message, the query calls give their documented neutral
+    answers, and the release calls are no-ops."""
+    import paper_2005_10680_gb300 as sp
+    lib = sp.load_library()
+    null = None
+    calls = {
+        "spamm_create": lambda: lib.spamm_create(null, 0, null),
+        "spamm_set_bound": lambda: lib.spamm_set_bound(null, 0),
+        "spamm_set_tau_table": lambda: lib.spamm_set_tau_table(null, 1.0, 0.9),
+        "spamm_mat_from_dense": lambda: lib.spamm_mat_from_dense(null, null, 64, 64, 64, 0.0, 0, null),
+        "spamm_mat_from_blocks": lambda: lib.spamm_mat_from_blocks(null, 64, 64, 0, null, null, null, 0,
+                                                                   null),
+        "spamm_mat_to_dense": lambda: lib.spamm_mat_to_dense(null, null, null, 64, 0),
+        "spamm_mat_info": lambda: lib.spamm_mat_info(null, null, null, null),
+        "spamm_mat_block_norms": lambda: lib.spamm_mat_block_norms(null, null, null),
+        "spamm_mat_block_map": lambda: lib.spamm_mat_block_map(null, null, null),
+        "spamm_cse": lambda: lib.spamm_cse(null, null, null, null, 0, null),
+        "spamm_multiply": lambda: lib.spamm_multiply(null, null, null, 1e-6, 0, null, null),
+        "spamm_multiply_tau": lambda: lib.spamm_multiply_tau(null, null, null, 0.0, 0, null, null),
+        "spamm_sp2_step": lambda: lib.spamm_sp2_step(null, null, 0, 1e-6, 0.0, 0, null, null),
+        "spamm_truncate": lambda: lib.spamm_truncate(null, null, 1e-6, 1, null),
+        "spamm_purify": lambda: lib.spamm_purify(null, null, 1, 1e-5, 10, null, null, null),
+        "spamm_purify_batched": lambda: lib.spamm_purify_batched(null, 0, null, null, 1e-5, 10, null, 1,
+                                                                 null, null, null),
+        "spamm_autotune": lambda: lib.spamm_autotune(null, null, 1e-6, 1, null),
+        "spamm_cse_search_noalloc": lambda: lib.spamm_cse_search_noalloc(null, null, 8, 1e-6, null, null,
+                                                                         null, null),
+    }
+    for name, call in calls.items():
+        assert call() == 1, name
+        assert lib.spamm_last_error(), name
+    assert lib.spamm_prec_supported(null, 0, 64) == 0
+    assert lib.spamm_ctx_launches(null) == 0
+    lib.spamm_destroy(null)
+    lib.spamm_mat_free(null)
