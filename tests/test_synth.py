@@ -55,3 +55,60 @@ def test_lattice_fock_off_diagonal_decay():
     g_abs = np.abs(P.F[off] / -np.exp(-a * d[off]) - 1.0) / 0.1
     # 1 + 0.1 g with g standard normal: |g| below 10 for every entry of this draw
     assert np.all(np.isfinite(g_abs)) and g_abs.max() < 10.0
+
+
+def _ratio_stats(F, centres, decay):
+    d = np.sqrt(((centres[:, None, :] - centres[None, :, :]) ** 2).sum(axis=-1))
+    off = ~np.eye(len(F), dtype=bool)
+    r = -F[off] / np.exp(-decay * d[off])
+    return float(r.mean()), float(r.std())
+
+
+def test_block_lattice_matches_the_dense_recipe():
+    """Without a cutoff the block generator draws the dense generator's distribution:
+    -F_ij / exp(-a d_ij) = 1 + 0.1 (g_ij + g_ji) / 2, mean 1 and deviation 0.1 / sqrt(2)."""
+    n, a = 512, 0.8
+    B = synth.lattice_fock_blocks(n, seed=4, decay=a, cutoff=1e9)
+    assert B.fill == 1.0
+    X = B.to_dense()
+    np.testing.assert_array_equal(X, X.T)
+    mean, std = _ratio_stats(X, B.centres, a)
+    assert abs(mean - 1.0) < 0.005 and abs(std - 0.1 / np.sqrt(2)) < 0.005
+    D = synth.lattice_fock(n, seed=4, decay=a, gap_mode="stagger")
+    mean_d, std_d = _ratio_stats(D.F, D.centres, a)
+    assert abs(mean_d - 1.0) < 0.005 and abs(std_d - 0.1 / np.sqrt(2)) < 0.005
+
+
+@pytest.mark.parametrize("n,cutoff", [(2048, 2.5), (4096, 3.0)])
+def test_block_lattice_cutoff_pattern_and_gap(n, cutoff):
+    B = synth.lattice_fock_blocks(n, seed=6, cutoff=cutoff)
+    X = B.to_dense()
+    np.testing.assert_array_equal(X, X.T)
+    d = np.sqrt(((B.centres[:, None, :] - B.centres[None, :, :]) ** 2).sum(axis=-1))
+    off = ~np.eye(n, dtype=bool)
+    assert np.all(X[off & (d > cutoff)] == 0.0)              # hard cutoff
+    assert np.all(X[off & (d <= cutoff)] != 0.0)
+    assert np.all(np.abs(X[off]) <= np.exp(-B.decay * d[off]) * 1.6)
+    # a block is stored exactly when it holds a pair of sites within the cutoff
+    nb = n // 64
+    dblk = d.reshape(nb, 64, nb, 64).min(axis=(1, 3))
+    stored = np.zeros((nb, nb), dtype=bool)
+    stored[B.brow, B.bcol] = True
+    np.testing.assert_array_equal(stored, dblk <= cutoff)
+    assert np.all(np.diff(B.brow.astype(np.int64) * nb + B.bcol) > 0)   # row-major order
+    # the staggered shift certifies the gap at n_occ (Gershgorin): eigenvalues agree
+    w = np.linalg.eigvalsh(X)
+    assert w[B.n_occ - 1] <= B.homo and w[B.n_occ] >= B.lumo and B.lumo - B.homo >= 0.1 - 1e-12
+    # the pattern alone is the same and the stream does not depend on the caller
+    Q = synth.lattice_fock_blocks(n, seed=6, cutoff=cutoff, pattern_only=True)
+    np.testing.assert_array_equal(Q.brow, B.brow)
+    np.testing.assert_array_equal(Q.bcol, B.bcol)
+    np.testing.assert_array_equal(synth.lattice_fock_blocks(n, seed=6, cutoff=cutoff).tiles, B.tiles)
+
+
+def test_large_lattice_block_fill():
+    """n = 262144 (65536 sites in a 64 x 32 x 32 box) at the default cutoff 6: about 3 %
+    of the 4096 x 4096 leaf blocks, about 5.5e5 tiles (18 GB of float64)."""
+    Q = synth.lattice_fock_blocks(262144, pattern_only=True)
+    assert 0.02 <= Q.fill <= 0.05
+    assert np.ptp(Q.centres, axis=0).round().tolist() == [63.0, 31.0, 31.0]
