@@ -46,7 +46,7 @@ WORKLOAD = ("SP2 purification (hybrid, Algorithm 5) of a 3D-lattice Fock matrix,
             "eps 1e-5")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1)
@@ -63,11 +63,33 @@ def parse():
     ap.add_argument("--protocol", action="store_true",
                     help="run the two-squares experiment instead of the purification bench")
     ap.add_argument("--deltas", default="1e-2,1e-4,1e-6,1e-8")
-    ap.add_argument("--bound", default="alg3", choices=["alg3", "flat"],
-                    help="error bound of the tau searches (Algorithm 3, or the flat bound)")
+    ap.add_argument("--bound", default="alg3", choices=["alg3", "flat", "spectral"],
+                    help="error bound of the tau searches (Algorithm 3, the flat bound, or the "
+                         "spectral-norm bound; the last only with --protocol)")
+    ap.add_argument("--tau-start", type=float, default=None,
+                    help="first tau candidate (default: the paper's list, 1)")
+    ap.add_argument("--tau-ratio", type=float, default=None,
+                    help="ratio of successive tau candidates (default: the paper's list, 0.9)")
     ap.add_argument("--input-cache", default=None,
                     help="npz file holding the generated input (written when absent)")
-    return ap.parse_args()
+    return check_args(ap, ap.parse_args(argv))
+
+
+def check_args(ap, args):
+    if args.bound == "spectral" and not args.protocol:
+        ap.error("--bound spectral certifies the spectral norm of one product; the purification "
+                 "keeps a Frobenius guarantee, so use it with --protocol")
+    if (args.tau_start is None) != (args.tau_ratio is None):
+        args.tau_start = 1.0 if args.tau_start is None else args.tau_start
+        args.tau_ratio = 0.9 if args.tau_ratio is None else args.tau_ratio
+    return args
+
+
+def tau_table_config(args):
+    """The candidate list of this run for the JSON line (None: the paper's list)."""
+    if args.tau_start is None:
+        return None
+    return {"start": args.tau_start, "ratio": args.tau_ratio, "length": 350}
 
 
 # --------------------------------------------------------------- inputs
@@ -278,6 +300,8 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     ctx = sp.Context(local, stream=stream)
     ctx.set_bound(args.bound)
+    if tau_table_config(args):
+        ctx.set_tau_table(args.tau_start, args.tau_ratio)
     form = args.form
     if form == "auto":
         form = "mixed" if ctx.supports("mixed", bs) else "fp64"
@@ -366,6 +390,7 @@ def run_ours(args, rank, world):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "n": n, "bs": bs, "eps": args.eps,
                        "variant": args.variant, "form": form, "bound": args.bound,
+                       **({"tau_table": tau_table_config(args)} if tau_table_config(args) else {}),
                        "l2": "inputs larger than L2 (2.1 GB per matrix), no flush",
                        "parallelism": f"replicas x{world}"},
             "spamm_ms": spamm_ms,
@@ -423,6 +448,7 @@ def approx_square(ctx, X, delta, variant, prec):
            "t_spamm_ms": 0.0 if variant == 1 else ms[6] - ms[1],
            "t_cse_ms": 0.0 if variant == 1 else ms[1],
            "t_trunc_ms": 0.0, "nnzb_product": Y.nnzb, "tau": rep["tau"],
+           "tau_index": rep["tau_index"], "cse_evals": rep["cse_evals"],
            "bound": rep["bound"], "bound_round": rep["bound_round"]}
     if variant in (1, 5):
         tr = ctx.truncate(Y, delta if variant == 1 else 0.5 * delta)
@@ -441,10 +467,25 @@ def fro_diff(A, B):
     return d
 
 
-def square_twice(ctx, D, delta, variant, prec):
+def norm2_diff(A, B):
+    """||A - B||_2 of two symmetric device matrices: the largest absolute eigenvalue of
+    the difference, read back densely (a check, not a step of the path)."""
+    import torch
+    a, b = A.to_torch(), B.to_torch()
+    a -= b
+    del b
+    a += a.T.clone()                      # exactly symmetric for the eigensolver
+    a *= 0.5
+    w = torch.linalg.eigvalsh(a)
+    del a
+    return float(w.abs().max())
+
+
+def square_twice(ctx, D, delta, variant, prec, spectral=False):
     """The paper's protocol for one (variant, delta): square D, square the result
     again at the same delta, time the second square and check it against the exact
-    float64 square of its input."""
+    float64 square of its input (in the spectral norm too when that is the norm
+    the searches certify)."""
     X1, _ = approx_square(ctx, D, delta, variant, prec)
     X2, out = approx_square(ctx, X1, delta, variant, prec)
     exact, _ = ctx.sp2_step(X1, 0, 0.0, 0.0, prec="fp64")
@@ -454,6 +495,9 @@ def square_twice(ctx, D, delta, variant, prec):
                             "product": 100.0 * out.pop("nnzb_product") / nb2,
                             "X_out": 100.0 * out.pop("nnzb_out") / nb2},
                 "err": err, "err_over_delta": err / delta})
+    if spectral:
+        err2 = norm2_diff(X2, exact)
+        out.update({"err_2": err2, "err_2_over_delta": err2 / delta})
     return out
 
 
@@ -471,13 +515,16 @@ def run_protocol(args):
                         variant=args.variant, prec=fastest, strict=False)
     del F
     ctx.set_bound(args.bound)
+    if tau_table_config(args):
+        ctx.set_tau_table(args.tau_start, args.tau_ratio)
     forms = [args.form] if args.form != "auto" else sorted({fastest, "fp64"})
     for form in forms:
         for delta in [float(x) for x in args.deltas.split(",")]:
             for name, v in PROTOCOL_VARIANTS:
-                out = square_twice(ctx, D, delta, v, form)
+                out = square_twice(ctx, D, delta, v, form, spectral=args.bound == "spectral")
                 line = {"protocol": "two squares of a converged D", "variant": name,
                         "algorithm": v, "delta": delta, "form": form, "bound_kind": args.bound,
+                        "tau_table": tau_table_config(args) or "paper",
                         "n": args.n, "bs": args.bs,
                         "D": f"SP2 purification (Algorithm {args.variant}, {fastest}) of the "
                              f"bench's Fock matrix, eps {args.eps}, {rep['iters']} iterations"}
