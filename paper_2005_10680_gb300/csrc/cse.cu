@@ -269,6 +269,12 @@ int cse_eval_impl(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const do
     int side = A->NB;
     int L = 0;
     while ((1 << L) < side) ++L;
+    if (side > 8192) {
+        // the first fold launches (side / 8)^3 CTAs, which must fit a 1-D grid
+        set_error("Algorithm 3: a padded grid of %d leaf blocks per side is above 8192; use "
+                  "the flat or spectral bound", side);
+        return SPAMM_ENOTSUP;
+    }
     if (L == 0) {
         // a single leaf triple
         ++ctx->launches;
