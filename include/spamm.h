@@ -168,6 +168,15 @@ int spamm_mat_from_blocks(spamm_ctx* ctx, int64_t n, int bs, int64_t nnzb, const
 int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* out, int64_t ld,
                        int out_on_device);
 
+/* The stored leaf blocks of m, the inverse of spamm_mat_from_blocks: the
+   nnzb blocks (spamm_mat_info) in row-major block order, block t at block row
+   brow[t] and block column bcol[t] (host arrays of nnzb entries), its bs x bs
+   entries row-major at tiles + t * bs * bs (host or device memory of nnzb * bs * bs
+   doubles, as `tiles_on_device` says; entries outside the n x n matrix are 0).
+   Blocks removed by truncation are not listed. SPAMM_EINVAL for a null argument. */
+int spamm_mat_to_blocks(spamm_ctx* ctx, const spamm_mat* m, int32_t* brow, int32_t* bcol,
+                        double* tiles, int tiles_on_device);
+
 /* Shape and storage: any pointer may be NULL. */
 int spamm_mat_info(const spamm_mat* m, int64_t* n, int* bs, int64_t* nnzb);
 

@@ -97,6 +97,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_prec_supported": ([vp, i32, i32], i32),
         "spamm_mat_from_dense": ([vp, vp, i64, i64, i32, d, i32, P(vp)], i32),
         "spamm_mat_to_dense": ([vp, vp, vp, i64, i32], i32),
+        "spamm_mat_to_blocks": ([vp, vp, _PI32, _PI32, vp, i32], i32),
         "spamm_mat_from_blocks": ([vp, i64, i32, i64, P(i32), P(i32), vp, i32, P(vp)], i32),
         "spamm_mat_info": ([vp, P(i64), P(i32), P(i64)], i32),
         "spamm_mat_block_norms": ([vp, vp, _PD], i32),
@@ -197,6 +198,18 @@ class Matrix:
         _check(_lib.spamm_mat_to_dense(self.ctx.handle, self.handle, out.data_ptr(), n, 1),
                "spamm_mat_to_dense")
         return out
+
+    def to_blocks(self):
+        """The stored leaf blocks, row-major: (brow, bcol, tiles) with tiles of shape
+        (nnzb, bs, bs) (the inverse of Context.from_blocks)."""
+        n, bs, nnzb = self.info()
+        brow = np.empty(nnzb, dtype=np.int32)
+        bcol = np.empty(nnzb, dtype=np.int32)
+        tiles = np.empty((nnzb, bs, bs))
+        _check(_lib.spamm_mat_to_blocks(self.ctx.handle, self.handle,
+                                        brow.ctypes.data_as(_PI32), bcol.ctypes.data_as(_PI32),
+                                        tiles.ctypes.data, 0), "spamm_mat_to_blocks")
+        return brow, bcol, tiles
 
     def to_host(self, out):
         """Write densely into a host buffer (numpy array or CPU torch tensor,

@@ -526,6 +526,56 @@ extern "C" int spamm_mat_from_blocks(spamm_ctx* ctx, int64_t n, int bs, int64_t 
     return SPAMM_OK;
 }
 
+extern "C" int spamm_mat_to_blocks(spamm_ctx* ctx, const spamm_mat* m, int32_t* brow,
+                                   int32_t* bcol, double* tiles, int tiles_on_device) {
+    if (!ctx || !m || (m->nnzb > 0 && (!brow || !bcol || !tiles))) {
+        set_error("spamm_mat_to_blocks: bad argument");
+        return SPAMM_EINVAL;
+    }
+    SP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const int64_t nb = m->nb, nb2 = nb * nb;
+    // the block map is the record of which blocks are live (truncation only edits it)
+    std::vector<int32_t> map((size_t)nb2);
+    SP_CUDA(cudaMemcpyAsync(map.data(), m->d_map, sizeof(int32_t) * (size_t)nb2,
+                            cudaMemcpyDeviceToHost, s));
+    SP_CUDA(cudaStreamSynchronize(s));
+    int64_t live = 0;
+    for (int64_t b = 0; b < nb2; ++b) live += map[(size_t)b] >= 0;
+    if (live != m->nnzb) {
+        set_error("spamm_mat_to_blocks: the block map holds %lld blocks, the matrix %lld",
+                  (long long)live, (long long)m->nnzb);
+        return SPAMM_ECUDA;
+    }
+    const size_t tile = (size_t)m->bs * m->bs;
+    const cudaMemcpyKind kind = tiles_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    // blocks in row-major order; runs of consecutive slots move in one copy
+    int64_t t = 0, run_t = 0, run_slot = -1, run_len = 0;
+    auto flush = [&]() -> cudaError_t {
+        if (run_len == 0) return cudaSuccess;
+        return cudaMemcpyAsync(tiles + (size_t)run_t * tile, m->d_tiles + (size_t)run_slot * tile,
+                               sizeof(double) * tile * (size_t)run_len, kind, s);
+    };
+    for (int64_t b = 0; b < nb2; ++b) {
+        const int32_t slot = map[(size_t)b];
+        if (slot < 0) continue;
+        brow[t] = (int32_t)(b / nb);
+        bcol[t] = (int32_t)(b % nb);
+        if (run_len > 0 && slot == run_slot + run_len) {
+            ++run_len;
+        } else {
+            SP_CUDA(flush());
+            run_t = t;
+            run_slot = slot;
+            run_len = 1;
+        }
+        ++t;
+    }
+    SP_CUDA(flush());
+    SP_CUDA(cudaStreamSynchronize(s));
+    return SPAMM_OK;
+}
+
 extern "C" int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* out, int64_t ld,
                                   int out_on_device) {
     if (!ctx || !m || !out || ld < m->n) {
