@@ -177,6 +177,14 @@ int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* out, int64_t 
 int spamm_mat_to_blocks(spamm_ctx* ctx, const spamm_mat* m, int32_t* brow, int32_t* bcol,
                         double* tiles, int tiles_on_device);
 
+/* Selected leaf blocks of m: block t of the request is (brow[t], bcol[t]) (host
+   arrays of count entries), written row-major to host memory tiles + t * bs * bs;
+   an absent block is written as zeros and present[t] (optional) says 1 for a stored
+   block, 0 for an absent one. For checking samples of matrices too large to export.
+   SPAMM_EINVAL for a null argument or a block outside the block grid. */
+int spamm_mat_get_blocks(spamm_ctx* ctx, const spamm_mat* m, int64_t count, const int32_t* brow,
+                         const int32_t* bcol, double* tiles, int32_t* present);
+
 /* Shape and storage: any pointer may be NULL. */
 int spamm_mat_info(const spamm_mat* m, int64_t* n, int* bs, int64_t* nnzb);
 

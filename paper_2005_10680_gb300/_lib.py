@@ -98,6 +98,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_mat_from_dense": ([vp, vp, i64, i64, i32, d, i32, P(vp)], i32),
         "spamm_mat_to_dense": ([vp, vp, vp, i64, i32], i32),
         "spamm_mat_to_blocks": ([vp, vp, _PI32, _PI32, vp, i32], i32),
+        "spamm_mat_get_blocks": ([vp, vp, i64, _PI32, _PI32, vp, _PI32], i32),
         "spamm_mat_from_blocks": ([vp, i64, i32, i64, P(i32), P(i32), vp, i32, P(vp)], i32),
         "spamm_mat_info": ([vp, P(i64), P(i32), P(i64)], i32),
         "spamm_mat_block_norms": ([vp, vp, _PD], i32),
@@ -210,6 +211,21 @@ class Matrix:
                                         brow.ctypes.data_as(_PI32), bcol.ctypes.data_as(_PI32),
                                         tiles.ctypes.data, 0), "spamm_mat_to_blocks")
         return brow, bcol, tiles
+
+    def get_blocks(self, brow, bcol):
+        """Selected leaf blocks (bs x bs each, zeros where absent) and a flag per block
+        saying whether it is stored."""
+        brow = np.ascontiguousarray(brow, dtype=np.int32)
+        bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+        count = len(brow)
+        bs = self.bs
+        tiles = np.empty((count, bs, bs))
+        present = np.empty(count, dtype=np.int32)
+        _check(_lib.spamm_mat_get_blocks(self.ctx.handle, self.handle, count,
+                                         brow.ctypes.data_as(_PI32), bcol.ctypes.data_as(_PI32),
+                                         tiles.ctypes.data, present.ctypes.data_as(_PI32)),
+               "spamm_mat_get_blocks")
+        return tiles, present.astype(bool)
 
     def to_host(self, out):
         """Write densely into a host buffer (numpy array or CPU torch tensor,

@@ -576,6 +576,39 @@ extern "C" int spamm_mat_to_blocks(spamm_ctx* ctx, const spamm_mat* m, int32_t* 
     return SPAMM_OK;
 }
 
+extern "C" int spamm_mat_get_blocks(spamm_ctx* ctx, const spamm_mat* m, int64_t count,
+                                    const int32_t* brow, const int32_t* bcol, double* tiles,
+                                    int32_t* present) {
+    if (!ctx || !m || count < 0 || (count > 0 && (!brow || !bcol || !tiles))) {
+        set_error("spamm_mat_get_blocks: bad argument");
+        return SPAMM_EINVAL;
+    }
+    const int64_t nb = m->nb;
+    for (int64_t t = 0; t < count; ++t)
+        if (brow[t] < 0 || brow[t] >= nb || bcol[t] < 0 || bcol[t] >= nb) {
+            set_error("spamm_mat_get_blocks: block %lld at (%d, %d) is outside the %lld x %lld "
+                      "block grid", (long long)t, brow[t], bcol[t], (long long)nb, (long long)nb);
+            return SPAMM_EINVAL;
+        }
+    SP_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = ctx->stream;
+    const size_t tile = (size_t)m->bs * m->bs;
+    for (int64_t t = 0; t < count; ++t) {
+        int32_t slot = -1;
+        SP_CUDA(cudaMemcpyAsync(&slot, m->d_map + (int64_t)brow[t] * nb + bcol[t], sizeof slot,
+                                cudaMemcpyDeviceToHost, s));
+        SP_CUDA(cudaStreamSynchronize(s));
+        if (present) present[t] = slot >= 0 ? 1 : 0;
+        if (slot >= 0)
+            SP_CUDA(cudaMemcpyAsync(tiles + (size_t)t * tile, m->d_tiles + (size_t)slot * tile,
+                                    sizeof(double) * tile, cudaMemcpyDeviceToHost, s));
+        else
+            memset(tiles + (size_t)t * tile, 0, sizeof(double) * tile);
+    }
+    SP_CUDA(cudaStreamSynchronize(s));
+    return SPAMM_OK;
+}
+
 extern "C" int spamm_mat_to_dense(spamm_ctx* ctx, const spamm_mat* m, double* out, int64_t ld,
                                   int out_on_device) {
     if (!ctx || !m || !out || ld < m->n) {

@@ -87,6 +87,8 @@ def test_entry_points_reject_null_handles_without_a_gpu():
                                                                    null),
         "spamm_mat_to_dense": lambda: lib.spamm_mat_to_dense(null, null, null, 64, 0),
         "spamm_mat_to_blocks": lambda: lib.spamm_mat_to_blocks(null, null, null, null, null, 0),
+        "spamm_mat_get_blocks": lambda: lib.spamm_mat_get_blocks(null, null, 1, null, null, null,
+                                                                  null),
         "spamm_mat_info": lambda: lib.spamm_mat_info(null, null, null, null),
         "spamm_mat_block_norms": lambda: lib.spamm_mat_block_norms(null, null, null),
         "spamm_mat_block_map": lambda: lib.spamm_mat_block_map(null, null, null),

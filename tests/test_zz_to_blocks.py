@@ -1,6 +1,7 @@
-"""spamm_mat_to_blocks, the inverse of spamm_mat_from_blocks, against the dense
-export: matrices built from an unordered block list (ragged edge included), SP2
-products, and the same products after truncation removed blocks."""
+"""spamm_mat_to_blocks, the inverse of spamm_mat_from_blocks, and
+spamm_mat_get_blocks against the dense export: matrices built from an unordered
+block list (ragged edge included), SP2 products, and the same products after
+truncation removed blocks."""
 import numpy as np
 import pytest
 
@@ -42,6 +43,18 @@ def test_blocks_round_trip(n):
     got = _assemble(n, r, c, T)
     np.testing.assert_array_equal(got, want)
     np.testing.assert_array_equal(got[:n, :n], M.to_numpy())
+    # selected blocks, stored and absent, the ragged corner among them
+    qi = np.array([nb - 1, 0] + [int(x) for x in g.integers(0, nb, 6)], dtype=np.int32)
+    qj = np.array([nb - 1, nb - 1] + [int(x) for x in g.integers(0, nb, 6)], dtype=np.int32)
+    Q, present = M.get_blocks(qi, qj)
+    stored = M.block_map()
+    for t in range(len(qi)):
+        i, j = int(qi[t]), int(qj[t])
+        assert present[t] == stored[i, j]
+        np.testing.assert_array_equal(Q[t], want[i * BS:(i + 1) * BS, j * BS:(j + 1) * BS])
+    with pytest.raises(sp.SpammError) as ei:
+        M.get_blocks([nb], [0])
+    assert ei.value.status == 1
     E = ctx.from_blocks(n, BS, [], [], np.zeros((0, BS, BS)))
     r, c, T = E.to_blocks()
     assert len(r) == len(c) == len(T) == 0
