@@ -34,6 +34,8 @@ Readings where the paper is silent (each one is a choice, not the paper's):
 * Stop when 2 (||C - X||_F + bound(C)) < eps / 2 with C the approximate
   square formed in the current step; the current X is returned (its distance
   to the nearest projector is at most 2 ||X^2 - X||_F).
+* n_occ = 0 and n_occ = n give D = 0 and D = I directly (no step): the gap
+  bounds of the step tolerances have no occupied (unoccupied) group to follow.
 
 Parity: pinned by tests/test_oracle_*.py; see the header of oracle.c.
 """
@@ -278,6 +280,10 @@ def purify(F, n_occ: int, eps: float, n_iter: int, homo: float, lumo: float,
     Algorithm 4 (variant=4, SpAMM only) or Algorithm 5 (variant=5, hybrid)."""
     F = _f64(F)
     n = F.shape[0]
+    if n_occ in (0, n):
+        # Eq. 1 with the chemical potential outside the spectrum: D = 0 or I exactly
+        D = np.eye(n) if n_occ == n else np.zeros((n, n))
+        return PurifyResult(D, 0, True, [], [], [], [], [])
     if lmin is None or lmax is None:
         lmin, lmax = gershgorin(F)
     width = lmax - lmin

@@ -3,6 +3,7 @@
 // and 5 with the SP2 polynomials).
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "common.cuh"
 #include "search.h"
@@ -544,6 +545,36 @@ extern "C" int spamm_truncate(spamm_ctx* ctx, spamm_mat* X, double delta, int sy
     return SPAMM_OK;
 }
 
+// The degenerate occupations, exactly: D = 0 when nothing is occupied and D = I when
+// everything is (Eq. 1 with the chemical potential below or above the whole spectrum).
+// No SP2 step is taken; the gap bounds play no part.
+static int purify_trivial(spamm_ctx* ctx, const spamm_mat* F, bool full, spamm_mat** D,
+                          spamm_purify_report* rep) {
+    const int bs = F->bs;
+    const int64_t nb = F->nb, n = F->n;
+    const int64_t count = full ? nb : 0;
+    std::vector<int32_t> idx((size_t)(count > 0 ? count : 1), 0);
+    std::vector<double> tiles((size_t)(count > 0 ? count : 1) * bs * bs, 0.0);
+    for (int64_t b = 0; b < count; ++b) {
+        idx[(size_t)b] = (int32_t)b;
+        for (int64_t r = 0; r < bs && b * bs + r < n; ++r)
+            tiles[((size_t)b * bs + (size_t)r) * bs + (size_t)r] = 1.0;
+    }
+    SP_TRY(spamm_mat_from_blocks(ctx, n, bs, count, idx.data(), idx.data(), tiles.data(), 0, D));
+    if (rep) {
+        rep->iters = 0;
+        rep->converged = 1;
+        rep->idem = 0.0;
+        rep->trace = full ? (double)n : 0.0;
+        rep->lmin = rep->lmax = 0.0;
+        rep->kept_total = rep->formed_total = rep->cand_total = 0;
+        rep->pipe_flops_total = 0.0;
+        rep->ms_total = 0.0;
+        for (int i = 0; i < 8; ++i) rep->ms_phase[i] = 0.0;
+    }
+    return SPAMM_OK;
+}
+
 extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, double eps,
                             int n_iter, const spamm_purify_opts* opts, spamm_mat** D,
                             spamm_purify_report* rep) {
@@ -561,6 +592,7 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
         return SPAMM_EINVAL;
     }
     *D = nullptr;
+    if (n_occ == 0 || n_occ == F->n) return purify_trivial(ctx, F, n_occ == F->n, D, rep);
     SP_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t s = ctx->stream;
     spamm_purify_report R;

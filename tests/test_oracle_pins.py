@@ -357,3 +357,15 @@ def test_flat_bound_between_true_error_and_algorithm3(orc, n, bs, seed):
         assert np.linalg.norm(C - exact) <= f * (1 + 1e-12) + 1e-14
     # non-increasing along the table
     assert np.all(np.diff(flat) <= 0)
+
+
+@pytest.mark.parametrize("n,bs", [(64, 16), (100, 32)])
+def test_purify_degenerate_occupations(orc, n, bs):
+    """Eq. 1 with nothing occupied gives D = 0 and with everything occupied D = I;
+    the eigendecomposition agrees, and no SP2 step is taken."""
+    P = synth.lattice_fock(n, seed=5, gap_mode="stagger")
+    for n_occ, want in ((0, np.zeros((n, n))), (n, np.eye(n))):
+        r = orc.purify(P.F, n_occ, 1e-5, 30, P.homo, P.lumo, bs=bs)
+        assert r.converged and r.iters == 0
+        np.testing.assert_array_equal(r.D, want)
+        np.testing.assert_allclose(orc.exact_density(P.F, n_occ), want, atol=1e-12)
