@@ -37,7 +37,8 @@ extern "C" {
 #define SPAMM_ENOTCONV 5     /* purification hit n_iter before the stop rule */
 #define SPAMM_ENOTSUP 6      /* parameter combination not supported (e.g. mixed form with bs != 64) */
 
-#define SPAMM_N_TAU 350      /* tau candidates: tau_1 = 1, tau_i = 0.9 tau_{i-1} */
+#define SPAMM_N_TAU 350      /* tau candidates: by default tau_1 = 1, tau_i = 0.9 tau_{i-1}
+                                (the experiments' list; see spamm_set_tau_table) */
 
 typedef struct spamm_ctx spamm_ctx;
 typedef struct spamm_mat spamm_mat;
