@@ -380,8 +380,7 @@ extern "C" int spamm_create(spamm_ctx** out, int device, void* cuda_stream) {
         return SPAMM_EINVAL;
     }
     SP_CUDA(cudaSetDevice(device));
-    spamm_ctx* c = new spamm_ctx();
-    memset(c, 0, sizeof(*c));
+    spamm_ctx* c = new spamm_ctx();   // value-initialised: every field zero, then its default
     c->device = device;
     c->hint_tau = -1;              // no previous selection yet
     c->hint_lmax = 0;
