@@ -111,3 +111,41 @@ def test_entry_points_reject_null_handles_without_a_gpu():
     assert lib.spamm_ctx_launches(null) == 0
     lib.spamm_destroy(null)
     lib.spamm_mat_free(null)
+
+
+def test_header_is_c_and_the_library_links_from_c(tmp_path):
+    """include/spamm.h compiles as strict C99 and a C program links against the
+    library and calls it (an argument error needs no GPU)."""
+    import shutil
+    import subprocess
+
+    import paper_2005_10680_gb300 as sp
+    if shutil.which("gcc") is None:
+        import pytest
+        pytest.skip("no C compiler")
+    lib = sp.library_path()
+    src = tmp_path / "use_spamm.c"
+    src.write_text(
+        "#include <stdio.h>\n#include \"spamm.h\"\n"
+        "int main(void) {\n"
+        "    spamm_ctx* ctx = NULL;\n"
+        "    spamm_mat* m = NULL;\n"
+        "    spamm_report rep;\n"
+        "    spamm_purify_opts opts;\n"
+        "    (void)rep; (void)opts; (void)m;\n"
+        "    int st = spamm_create(NULL, 0, NULL);\n"
+        "    if (st != SPAMM_EINVAL) return 1;\n"
+        "    st = spamm_multiply(ctx, NULL, NULL, 1e-6, SPAMM_MIXED, &m, NULL);\n"
+        "    if (st != SPAMM_EINVAL) return 2;\n"
+        "    printf(\"%s\\n\", spamm_last_error());\n"
+        "    return 0;\n"
+        "}\n")
+    exe = tmp_path / "use_spamm"
+    libdir = os.path.dirname(lib)
+    name = os.path.basename(lib)[3:-3]                    # libNAME.so -> NAME
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                           "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir,
+                           "-l" + name, "-Wl,-rpath," + libdir, "-o", str(exe)])
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out
+    assert "spamm_multiply" in out.stdout
