@@ -25,7 +25,7 @@ def pytest_collection_modifyitems(config, items):
         return
     skip = pytest.mark.skip(reason="full-size configuration: run with --run-large")
     for item in items:
-        if "large" in item.keywords:
+        if item.get_closest_marker("large") is not None:
             item.add_marker(skip)
 
 
