@@ -25,3 +25,24 @@ def test_tuned_list_options():
     assert bench.tau_table_config(args) == {"start": 8.0, "ratio": 0.9, "length": 350}
     args = bench.parse(["--tau-ratio", "0.95"])
     assert bench.tau_table_config(args) == {"start": 1.0, "ratio": 0.95, "length": 350}
+
+
+def test_reference_arm_line_on_a_small_case():
+    """The oracle arm's JSON line (run on the CPU, rank 0): impl, the arm's metric and
+    unit, a cpu_baseline describing the sample, and an e2e entry with no copies."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--n", "512", "--sample-n", "256", "--steps", "1", "--warmup", "0"],
+                         capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "ms" and line["higher_is_better"] is False and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "ms", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
