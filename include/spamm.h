@@ -127,8 +127,9 @@ int64_t spamm_ctx_launches(const spamm_ctx* ctx);
 int spamm_prec_supported(const spamm_ctx* ctx, spamm_prec prec, int bs);
 
 /* Select the bound for all later searches and bound evaluations on ctx (spamm_cse,
-   spamm_multiply, spamm_sp2_step, spamm_purify). SPAMM_EINVAL for an unknown
-   value. */
+   spamm_multiply, spamm_multiply_tau, spamm_sp2_step, spamm_purify,
+   spamm_purify_batched; the purification drivers accept ALG3 and FLAT only).
+   SPAMM_EINVAL for an unknown value. */
 int spamm_set_bound(spamm_ctx* ctx, spamm_bound bound);
 
 /* Replace the context's tau candidates by tau_1 = start, tau_i = ratio tau_{i-1}
@@ -321,8 +322,9 @@ int spamm_autotune(spamm_ctx* ctx, const spamm_mat* X, double delta, int allow_m
    n, n_occ[i] and opts[i]; eps and n_iter shared) purified concurrently by
    `workers` host threads, each with its own CUDA stream on ctx's device, so the
    kernels of different problems overlap. Each problem follows spamm_purify
-   exactly (identical results), with ctx's error bound (spamm_set_bound). Work
-   pending on ctx's stream is finished first. Outputs: D[i] (caller frees), reps[i] (optional;
+   exactly (identical results), with ctx's error bound (spamm_set_bound; the
+   spectral bound is refused with SPAMM_EINVAL, as by spamm_purify) and ctx's tau
+   candidates (spamm_set_tau_table). Work pending on ctx's stream is finished first. Outputs: D[i] (caller frees), reps[i] (optional;
    its step-log pointers are used as given), status[i] = spamm_purify's status.
    Returns SPAMM_OK when every problem returned SPAMM_OK or SPAMM_ENOTCONV,
    else the status of a failing problem. */
