@@ -296,7 +296,9 @@ typedef struct {
    D is returned (caller frees). SPAMM_ENOTCONV when n_iter steps did not
    satisfy the stop rule (D and the report are still filled). The degenerate
    occupations are exact without any step: n_occ = 0 gives D = 0 and n_occ = n
-   gives D = I (iters = 0, converged = 1; homo/lumo are not used). */
+   gives D = I (iters = 0, converged = 1; homo/lumo are not used). SPAMM_EINVAL
+   when ctx's bound is SPAMM_BOUND_SPECTRAL: the step tolerances bound a Frobenius
+   subspace error. */
 int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, double eps, int n_iter,
                  const spamm_purify_opts* opts, spamm_mat** D, spamm_purify_report* rep);
 
