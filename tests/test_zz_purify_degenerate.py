@@ -24,9 +24,11 @@ def test_degenerate_occupations(orc, prec):
         assert rep["trace"] == n_occ and rep["idem"] == 0.0
         assert D.nnzb == blocks
         np.testing.assert_array_equal(D.to_numpy(), want)
-    out = ctx.purify_batched([F, F, F], [0, n, P.n_occ], 1e-5, 60, [P.homo] * 3, [P.lumo] * 3,
-                             prec=prec, workers=2)
+    Q = synth.lattice_fock(256, seed=9, gap_mode="stagger")       # an ordinary problem beside them
+    G = ctx.from_dense(Q.F, 64)
+    out = ctx.purify_batched([F, F, G], [0, n, Q.n_occ], 1e-5, 60, [P.homo, P.homo, Q.homo],
+                             [P.lumo, P.lumo, Q.lumo], prec=prec, workers=2)
     np.testing.assert_array_equal(out[0][0].to_numpy(), zero)
     np.testing.assert_array_equal(out[1][0].to_numpy(), eye)
     assert out[2][1]["status"] == 0 and out[2][1]["converged"]
-    assert np.linalg.norm(out[2][0].to_numpy() - orc.exact_density(P.F, P.n_occ)) < 1e-5
+    assert np.linalg.norm(out[2][0].to_numpy() - orc.exact_density(Q.F, Q.n_occ)) < 1e-5
