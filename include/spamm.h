@@ -241,14 +241,20 @@ int spamm_truncate(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric,
    Frobenius norms of A and B, row-major (entry i*nb + k is ||A_ik||_F; 0 for an
    absent block). Outputs (device pointers, each may be NULL): *d_index = the
    0-based index of the chosen candidate (-1: none, exact product), *d_tau =
-   that tau (0 for none), *d_bound = its Algorithm 3 bound. The search is the
-   one spamm_multiply runs (same kernels, same result), ordered on cuda_stream
-   (a cudaStream_t, NULL for the default stream); the call returns without
-   waiting for it.
+   that tau (0 for none), *d_bound = its Algorithm 3 bound. The search always
+   uses the default candidate list (tau_1 = 1, tau_i = 0.9 tau_{i-1}) and
+   Algorithm 3's bound with float64 leaf products (no rounding charge), so it
+   selects what spamm_multiply selects with SPAMM_FP64 on a context with the
+   default list and SPAMM_BOUND_ALG3 (the same fold, bit for bit); a context with
+   spamm_set_tau_table, another bound, or SPAMM_MIXED (whose leaves carry the
+   slicing charge) may select another tau. It is ordered on cuda_stream (a
+   cudaStream_t, NULL for the default stream); the call returns without waiting
+   for it.
    Scratch: one fixed device array of about 516 KB that every device loading the
    library holds until exit; nb > 256 is rejected with SPAMM_EINVAL. Nothing is
    allocated. The first call on each device resolves that array's address and
-   writes the tau table into it, so make that first call before any stream
+   writes the tau table into it, then waits for cuda_stream to finish that write
+   (once per device, under a lock), so make that first call before any stream
    capture. Every call shares the array: calls that overlap on the GPU (on
    different streams, or from several threads) race and must be serialised by
    the caller. */

@@ -526,7 +526,8 @@ int cse_search_scratch(cudaStream_t s, const double* nA, const double* nB, int n
         }
         k_bisect_step<<<1, 1, 0, s>>>(sc, d_tau_table, delta);
     }
-    return cudaGetLastError() == cudaSuccess ? SPAMM_OK : SPAMM_ECUDA;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SPAMM_OK : cuda_fail(e, "cse search", __FILE__, __LINE__);
 }
 
 }  // namespace spamm

@@ -7,6 +7,8 @@
 // only ever sees a host-side stand-in for that array's name, so the device
 // address is looked up once per device with cudaGetSymbolAddress (with that
 // device current) and passed to the kernels.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace spamm {
@@ -48,15 +50,21 @@ __global__ void k_noalloc_result(const NoAllocScratch* s, int32_t* index, double
     if (bound) *bound = none ? 0.0 : s->sc.err_at_hi;
 }
 
-// One-time set-up on the current device: resolve the array's device address and
-// write the tau table into it (ordered on the caller's stream).
+// One-time set-up of device `dev` (the current device): resolve the array's device
+// address and write the tau table into it. It runs once per device under a lock, and
+// it waits for the table on the caller's stream before the address is published, so a
+// later call on any stream (or any host thread) finds the table written.
+std::mutex g_noalloc_init;
+
 int noalloc_setup(int dev, cudaStream_t s, NoAllocScratch** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_init);
     if (!g_noalloc_addr[dev]) {
         NoAllocScratch* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress((void**)&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress", __FILE__, __LINE__);
         k_noalloc_tau_table<<<1, 1, 0, s>>>(p);
         e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "tau table", __FILE__, __LINE__);
         g_noalloc_addr[dev] = p;
     }

@@ -29,8 +29,11 @@ def test_noalloc_search_matches_spamm_multiply_twice():
     import paper_2005_10680_gb300 as sp
     ctx = sp.Context(0)
     lib = sp.load_library()
+    # the last case has nb = 200 leaf blocks per side: its first fold fills every
+    # entry of the scratch's first level buffer and it folds one level more
     cases = [(synth.banded_decay(1000, 31, length=40.0), 64, 1e-6),
-             (synth.random_decaying(700, 32, length=30.0), 32, 1e-4)]
+             (synth.random_decaying(700, 32, length=30.0), 32, 1e-4),
+             (synth.banded_decay(6400, 33, length=40.0), 32, 1e-6)]
     for X, bs, delta in cases:
         G = ctx.from_dense(X, bs)
         _, rep = ctx.multiply(G, G, delta, prec="fp64")
