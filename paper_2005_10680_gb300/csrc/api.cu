@@ -602,9 +602,17 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
     R.kept_total = R.cand_total = R.formed_total = 0;
     R.pipe_flops_total = 0.0;
     for (int i = 0; i < 8; ++i) R.ms_phase[i] = 0.0;
-    cudaEvent_t e0, e1;
-    SP_CUDA(cudaEventCreate(&e0));
-    SP_CUDA(cudaEventCreate(&e1));
+    // both events are destroyed on every path out of this function
+    struct EventPair {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ~EventPair() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+        }
+    } ev;
+    SP_CUDA(cudaEventCreate(&ev.e0));
+    SP_CUDA(cudaEventCreate(&ev.e1));
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     cudaEventRecord(e0, s);
 
     double lmin = opts->lmin, lmax = opts->lmax;
@@ -714,8 +722,6 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
     cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (st != SPAMM_OK) {
         spamm_mat_free(X);
         return st;
