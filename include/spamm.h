@@ -51,10 +51,9 @@ typedef struct spamm_mat spamm_mat;
 typedef enum { SPAMM_FP64 = 0, SPAMM_MIXED = 1 } spamm_prec;
 
 /* Error bound used by the tau searches (and reported) on a context.
-   ALG3: Algorithm 3's hierarchical bound (the default). Its evaluation needs the
-   leaf grid padded to a power of two to be at most 8192 blocks per side (n up to
-   524288 at bs = 64); larger grids give SPAMM_ENOTSUP (FLAT and SPECTRAL have no
-   such limit).
+   ALG3: Algorithm 3's hierarchical bound (the default). Its evaluation visits the
+   live node triples of the recursion only (both nodes hold a stored block), so
+   its cost follows the candidate products, not the cube of the block grid.
    FLAT: the one-level bound sqrt(sum_ij (sum_k e_ikj)^2) over the same leaf terms
    e_ikj (a skipped product's norm product, a formed one's slicing charge). It is
    still an upper bound on ||E||_F (triangle inequality per block) and never

@@ -71,6 +71,28 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     int64_t n_cand = 0, n_tasks = 0, n_kept = 0;
     spamm_mat* C = nullptr;
     int st = SPAMM_OK;
+    // the product's sparse structures: row lists of both operands (planner, one-level
+    // bounds) and the live tree of Algorithm 3, built once from the block patterns
+    BlockLists rowsA, rowsB;
+    CseTree tree;
+    st = lists_build_i32(ctx, A->d_map, A->nb, A->nb, 0, &rowsA);
+    if (st == SPAMM_OK) st = lists_build_i32(ctx, B->d_map, B->nb, B->nb, 0, &rowsB);
+    if (st == SPAMM_OK && ctx->bound == SPAMM_BOUND_ALG3)
+        st = tree_build(ctx, A->d_map, B->d_map, A->nb, &tree);
+    auto release_structs = [&]() {
+        rowsA.free(s);
+        rowsB.free(s);
+        tree.free(s);
+    };
+    if (st != SPAMM_OK) {
+        release_structs();
+        dfree(nsym, s);
+        return st;
+    }
+    BoundCtx bc;
+    bc.tree = &tree;
+    bc.rowsA = &rowsA;
+    bc.rowsB = &rowsB;
     double err_charge = 0.0;
     int lmax_used = 0;
     MixedPrep mp;
@@ -78,6 +100,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     if (use_mixed) {
         st = mixed_prepare(ctx, A, B, sym, &mp);
         if (st != SPAMM_OK) {
+            release_structs();
             dfree(nsym, s);
             return st;
         }
@@ -92,7 +115,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
             ChargeData ch = mixed_charge(A, B, nA, nB, mp, L);
             ++ctx->launches;
             k_set_tau<<<1, 1, 0, s>>>(sc, 0.0);
-            int r = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_charge, ch);
+            int r = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_charge, ch, bc);
             if (r != SPAMM_OK) return r;
             cudaMemcpyAsync(ec, &sc->err_charge, 8, cudaMemcpyDeviceToHost, s);
             cudaStreamSynchronize(s);
@@ -144,13 +167,13 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         ChargeData ch = use_mixed ? mixed_charge(A, B, nA, nB, mp, lmax_used) : ChargeData();
         int ev2 = 0;
         if (search) {
-            st = cse_search(ctx, A, nA, nB, delta, ch, &ev2, ctx->hint_tau);
+            st = cse_search(ctx, A, nA, nB, delta, ch, bc, &ev2, ctx->hint_tau);
             ++ctx->launches;
             k_select_tau<<<1, 1, 0, s>>>(sc, ctx->d_tau, SPAMM_N_TAU);
         } else {
             ++ctx->launches;
             k_set_tau<<<1, 1, 0, s>>>(sc, tau);
-            st = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_at_hi, ch);
+            st = cse_eval(ctx, A, nA, nB, &sc->tau_sel, &sc->err_at_hi, ch, bc);
             ev2 = 1;
         }
         evals += ev2;
@@ -166,7 +189,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     } else if (st == SPAMM_OK) {
         Plan plan;
         st = plan_build_impl(ctx, A, B, nA, nB, &sc->tau_sel, mode ? A : nullptr, mode == 2, sym,
-                             &plan, &C);
+                             rowsA, rowsB, &plan, &C);
         cudaEventRecord(ctx->ev[EV_PLAN1], s);
         int64_t nw = plan.n_work > 0 ? plan.n_work : 1;
         if (st == SPAMM_OK) st = dalloc((void**)&parts, sizeof(double) * 3 * nw, s);
@@ -189,6 +212,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         plan_free(&plan, s);
     }
     dfree(nsym, s);
+    release_structs();
     cudaEventRecord(ctx->ev[EV_END], s);
     DevScalars h;
     if (st == SPAMM_OK) {

@@ -174,13 +174,65 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
                         int mode, int sym, spamm_mat** C_out, int64_t* n_cand, int64_t* n_kept,
                         int64_t* n_formed, int64_t* n_pairs);
 
+// Sorted lists of the stored entries of a dense rows x cols block map (row-major;
+// an entry is stored when map[r * cols + c] >= 0): one list per row, or one per
+// column when built by column. List q holds idx[ptr[q] .. ptr[q + 1]), ascending.
+struct BlockLists {
+    int n = 0;                  // number of lists
+    int64_t total = 0;          // entries over all lists
+    int64_t* d_ptr = nullptr;   // [n + 1]
+    int32_t* d_idx = nullptr;   // [total]
+    void free(cudaStream_t s) {
+        dfree(d_ptr, s);
+        dfree(d_idx, s);
+        d_ptr = nullptr;
+        d_idx = nullptr;
+    }
+};
+int lists_build_i32(spamm_ctx* ctx, const int32_t* map, int rows, int cols, int by_col,
+                    BlockLists* out);
+int lists_build_i64(spamm_ctx* ctx, const int64_t* map, int rows, int cols, int by_col,
+                    BlockLists* out);
+
+// The live part of Algorithm 3's recursion for C = A B, built once per product
+// (it depends on the block patterns only, not on tau). A node triple (I, K, J) at
+// level l (2^l leaf blocks per side) is live when A's node (I, K) and B's node
+// (K, J) both hold a stored block. Level l's live triples are listed so that the
+// children of one level-(l + 1) triple are consecutive, in the child order
+// b = k + 2 i + 4 j of the recursion's fold; a node's 8-bit mask says which
+// children are live. Level 1 also keeps its coordinates, from which the leaf
+// terms are computed. Folding the lists level by level computes exactly what a
+// fold of the whole padded cube computes (absent children are zeros there),
+// in work proportional to the live triples.
+constexpr int TREE_MAXL = 22;
+struct CseTree {
+    int L = 0;                          // 2^L >= nb
+    int nb = 0;
+    int64_t count[TREE_MAXL + 1] = {};  // live triples per level (count[L] <= 1)
+    int64_t leaves = 0;                 // live leaf triples (candidate products)
+    uint64_t* coord1 = nullptr;         // level-1 triples, I << 42 | K << 21 | J
+    uint8_t* mask[TREE_MAXL + 1] = {};  // child masks, levels 1..L
+    int64_t* cstart[TREE_MAXL + 1] = {};// levels 2..L: first child in level l - 1's list
+    double* buf[2] = {nullptr, nullptr};// values of a fold, by level parity
+    void free(cudaStream_t s);
+};
+int tree_build(spamm_ctx* ctx, const int32_t* mapA, const int32_t* mapB, int nb, CseTree* t);
+
 // CSE evaluation of one tau held in device memory (*d_tau_ptr); result into *d_err
 // nA, nB: the leaf norm maps to use (the matrices' own, or a symmetrised copy)
+// The bound's structures of one product: the live tree (Algorithm 3) and the row
+// lists of both operands (the one-level and spectral bounds, and the planners).
+struct BoundCtx {
+    const CseTree* tree = nullptr;
+    const BlockLists* rowsA = nullptr;
+    const BlockLists* rowsB = nullptr;
+};
 int cse_eval(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
-             const double* d_tau_ptr, double* d_err, const ChargeData& ch);
+             const double* d_tau_ptr, double* d_err, const ChargeData& ch, const BoundCtx& bc);
 // bisection for the tau index; fills DevScalars lo/hi/err_at_hi
 int cse_search(spamm_ctx* ctx, const spamm_mat* A, const double* nA, const double* nB,
-               double delta, const ChargeData& ch, int* evals, int hint = -1);
+               double delta, const ChargeData& ch, const BoundCtx& bc, int* evals,
+               int hint = -1);
 // out[i,j] = in[min(i,j), max(i,j)]: a bitwise-symmetric copy of a norm map
 int sym_norms(spamm_ctx* ctx, const double* in, int nb, double* out);
 int tau_table_install(spamm_ctx* ctx, const double* h);
@@ -208,13 +260,9 @@ struct Plan {
 // as output blocks too (SP2 step 2X - X^2).
 int plan_build_impl(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
                     const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
-                    int sym, Plan* plan, spamm_mat** C_out);
+                    int sym, const BlockLists& rowsA, const BlockLists& rowsB, Plan* plan,
+                    spamm_mat** C_out);
 void plan_free(Plan* plan, cudaStream_t s);
-// block-level keep counts (cnt), work flags (wf) and output flags (of) over the nb x nb
-// blocks; ch->lmax > 0 applies the mixed keep rule (charge below the norm product)
-int plan_count_blocks(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, const double* nA,
-                      const double* nB, const double* d_tau, const spamm_mat* X, int mode_dbl,
-                      int sym, int32_t* cnt, int32_t* wf, int32_t* of);
 // mapC[b] = out slot for every flagged block, and the slot -> block coordinates
 int plan_write_out_map(spamm_ctx* ctx, const int32_t* of, const int64_t* oidx, int nb,
                        spamm_mat* C);

@@ -78,14 +78,17 @@ __global__ void k_block_rowmax(const double* __restrict__ tiles, const int32_t* 
     }
 }
 
-// exponent of every row (columns when transpose): max |x| < 2^e
+// exponent of every row (columns when transpose): max |x| < 2^e, over the stored
+// blocks of the block row (block column) from its list
 __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __restrict__ map,
-                            int nb, int transpose, int32_t* __restrict__ expo) {
+                            int nb, int transpose, const int64_t* __restrict__ lptr,
+                            const int32_t* __restrict__ lidx, int32_t* __restrict__ expo) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nb * MX_BS) return;
     const int rb = (int)(r / MX_BS), rr = (int)(r % MX_BS);
     double m = 0.0;
-    for (int o = 0; o < nb; ++o) {
+    for (int64_t q = lptr[rb]; q < lptr[rb + 1]; ++q) {
+        const int o = lidx[q];
         const int32_t s = transpose ? map[(int64_t)o * nb + rb] : map[(int64_t)rb * nb + o];
         if (s >= 0) m = fmax(m, rmax[(int64_t)s * 64 + rr]);
     }
@@ -264,19 +267,23 @@ __global__ void k_pair_index(const int32_t* __restrict__ flag, int64_t* __restri
     if (e < n && !flag[e]) idx[e] = -1;
 }
 
-// zero the half of every pair tile whose block is not stored (one CTA per (I, k))
+// zero the half of every pair tile whose block is not stored (a CTA per (I, k) at a
+// time, over a grid-stride loop; absent pairs are passed over)
 __global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb, int transpose,
-                                    const int64_t* __restrict__ idx, uint8_t* __restrict__ pairs) {
-    const int64_t e = blockIdx.x;
-    const int I = (int)(e / nb), k = (int)(e % nb);
-    const int64_t pi = idx[e];
-    if (pi < 0) return;
-    for (int half = 0; half < 2; ++half) {
-        if (pair_block(map, nb, transpose, 2 * I + half, k) >= 0) continue;
-        uint8_t* base = pairs + pi * (int64_t)PAIR_BYTES + half * CHUNK;
-        for (int o = threadIdx.x; o < KCH * MX_S * (CHUNK / 16); o += blockDim.x) {
-            const int ch = o / (CHUNK / 16), w = o % (CHUNK / 16);   // ch: (K chunk, slice)
-            *reinterpret_cast<uint4*>(base + (int64_t)ch * 2 * CHUNK + w * 16) = make_uint4(0, 0, 0, 0);
+                                    const int64_t* __restrict__ idx, int64_t ne,
+                                    uint8_t* __restrict__ pairs) {
+    for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
+        const int64_t pi = idx[e];
+        if (pi < 0) continue;
+        const int I = (int)(e / nb), k = (int)(e % nb);
+        for (int half = 0; half < 2; ++half) {
+            if (pair_block(map, nb, transpose, 2 * I + half, k) >= 0) continue;
+            uint8_t* base = pairs + pi * (int64_t)PAIR_BYTES + half * CHUNK;
+            for (int o = threadIdx.x; o < KCH * MX_S * (CHUNK / 16); o += blockDim.x) {
+                const int ch = o / (CHUNK / 16), w = o % (CHUNK / 16);   // ch: (K chunk, slice)
+                *reinterpret_cast<uint4*>(base + (int64_t)ch * 2 * CHUNK + w * 16) =
+                    make_uint4(0, 0, 0, 0);
+            }
         }
     }
 }
@@ -307,9 +314,13 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
         dfree(tot, s);
         SP_TRY(dalloc((void**)&out->pairs, (size_t)(npairs > 0 ? npairs : 1) * PAIR_BYTES, s));
         if (npairs > 0) {
+            const int64_t want = (ne + 7) / 8;
+            const unsigned grid = (unsigned)(want < 8 * (int64_t)ctx->num_sms
+                                                 ? want
+                                                 : 8 * (int64_t)ctx->num_sms);
             ++ctx->launches;
-            k_pair_zero_missing<<<(unsigned)ne, 256, 0, s>>>(X->d_map, nb, transpose, out->pair_idx,
-                                                             out->pairs);
+            k_pair_zero_missing<<<grid, 256, 0, s>>>(X->d_map, nb, transpose, out->pair_idx, ne,
+                                                     out->pairs);
         }
     }
     SP_TRY(dalloc((void**)&out->p0, (size_t)ns, s));
@@ -324,8 +335,11 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
                                                            nullptr, rmax);
     }
     const int64_t rows = (int64_t)X->nb * MX_BS;
+    BlockLists lists;   // the stored blocks of every block row (block column)
+    SP_TRY(lists_build_i32(ctx, X->d_map, X->nb, X->nb, transpose, &lists));
     ++ctx->launches;
     k_exponents<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(rmax, X->d_map, X->nb, transpose,
+                                                               lists.d_ptr, lists.d_idx,
                                                                out->expo);
     if (X->nslots > 0) {
         ++ctx->launches;
@@ -334,6 +348,7 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
                                                     out->p0, out->sn, out->tn);
     }
     SP_CHECK_LAUNCH();
+    lists.free(s);
     dfree(rmax, s);
     return SPAMM_OK;
 }
@@ -357,6 +372,10 @@ struct Raster {
     int np, it, jt, nsj;
     __host__ __device__ int64_t size() const {
         return (int64_t)((np + it - 1) / it) * it * (int64_t)nsj * jt;
+    }
+    __device__ int64_t index(int I, int J) const {
+        const int64_t st = (int64_t)(I / it) * nsj + J / jt;
+        return st * ((int64_t)it * jt) + (int64_t)(I % it) * jt + J % jt;
     }
     __device__ bool unswizzle(int64_t b, int* I, int* J) const {
         const int64_t per = (int64_t)it * jt;
@@ -400,114 +419,160 @@ __device__ __forceinline__ int n_level_pairs(int pa, int qb, int L) {
     return n;
 }
 
+// Tiles are planned per pair row I (one CTA): the k of A's pair row (pair tile (I, k)
+// stored) in increasing k, and for each k the J of the B operand's pair tiles (J, k)
+// from the list of that k; only these k can trigger (elsewhere a pair maximum is
+// 0). The work is proportional to the candidate tile products plus np per pair row.
+
 // per tile: number of tasks, whether it has outputs, the output pattern, and the
 // candidate / kept triple counts of the full product (counters[0], counters[1])
-__global__ void k_tile_count(TilePlan tp, Raster rs, const double* __restrict__ d_tau,
-                             int32_t* __restrict__ cnt, int32_t* __restrict__ wflag,
-                             int32_t* __restrict__ out_flag,
-                             unsigned long long* __restrict__ counters) {
-    const int nb = tp.nb;
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256)
+k_tile_rows_count(TilePlan tp, Raster rs, const int64_t* __restrict__ ptrA,
+                  const int32_t* __restrict__ idxA, const int64_t* __restrict__ ptrK,
+                  const int32_t* __restrict__ idxK, const double* __restrict__ d_tau,
+                  int32_t* __restrict__ cnt, int32_t* __restrict__ wflag,
+                  int32_t* __restrict__ out_flag, unsigned long long* __restrict__ counters) {
+    extern __shared__ int32_t shp[];
+    const int np = rs.np, nb = tp.nb;
+    int32_t* tcnt = shp;        // [np] triggered k per tile (I, J)
+    int32_t* fbits = shp + np;  // [np] blocks of the tile with a formed product
+    const int I = blockIdx.x, t = threadIdx.x;
+    const int i0 = 2 * I;
+    for (int J = t; J < np; J += blockDim.x) tcnt[J] = fbits[J] = 0;
+    __syncthreads();
+    const double tau = *d_tau;
     unsigned long long cand = 0, kept = 0;
-    int c = 0, work = 0;
-    int I = 0, J = 0;
-    if (b < rs.size() && rs.unswizzle(b, &I, &J) && (!tp.sym || I <= J)) {
-        const double tau = *d_tau;
-        const int i0 = 2 * I, j0 = 2 * J;
-        int f = 0;   // bit 2h + c: block (i0 + h, j0 + c) has a formed product
-        unsigned long long cd = 0, kp = 0;
-        for (int k = 0; k < nb; ++k) {
-            const double a0 = nrm(tp.nA, nb, i0, k), a1 = nrm(tp.nA, nb, i0 + 1, k);
+    const int64_t qa1 = ptrA[I + 1];
+    for (int64_t q = ptrA[I]; q < qa1; ++q) {
+        const int k = idxA[q];
+        const double a0 = nrm(tp.nA, nb, i0, k), a1 = nrm(tp.nA, nb, i0 + 1, k);
+        const double ra = fmax(a0, a1);
+        const int64_t r1 = ptrK[k + 1];
+        for (int64_t r = ptrK[k] + t; r < r1; r += blockDim.x) {
+            const int J = idxK[r];
+            if (tp.sym && J < I) continue;
+            const int j0 = 2 * J;
             const double b0 = nrm(tp.nB, nb, k, j0), b1 = nrm(tp.nB, nb, k, j0 + 1);
             const double p[4] = {a0 * b0, a0 * b1, a1 * b0, a1 * b1};
-            const double m = fmax(a0, a1) * fmax(b0, b1);
+            const double m = ra * fmax(b0, b1);
             const bool trig = m > 0.0 && m >= tau;
+            int f = 0;
+            unsigned long long cd = 0, kp = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                cd += p[q] > 0.0;
-                kp += p[q] > 0.0 && p[q] >= tau;
-                if (trig && p[q] > 0.0) f |= 1 << q;
+            for (int e = 0; e < 4; ++e) {
+                cd += p[e] > 0.0;
+                kp += p[e] > 0.0 && p[e] >= tau;
+                if (trig && p[e] > 0.0) f |= 1 << e;
             }
-            c += trig;
+            const unsigned long long mult = (tp.sym && I < J) ? 2 : 1;
+            cand += mult * cd;
+            kept += mult * kp;
+            if (trig) {
+                atomicAdd(&tcnt[J], 1);
+                atomicOr(&fbits[J], f);
+            }
         }
+    }
+    __syncthreads();
+    for (int J = (tp.sym ? I : 0) + t; J < np; J += blockDim.x) {
+        const int j0 = 2 * J;
         const bool mirror = tp.sym && I < J;
-        cand = mirror ? 2 * cd : cd;
-        kept = mirror ? 2 * kp : kp;
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + (q >> 1), j = j0 + (q & 1);
+        const int f = fbits[J];
+        int work = 0;
+        for (int e = 0; e < 4; ++e) {
+            const int i = i0 + (e >> 1), j = j0 + (e & 1);
             if (i >= nb || j >= nb) continue;
-            const bool o = ((f >> q) & 1) || (tp.mapX && tp.mapX[(int64_t)i * nb + j] >= 0);
+            const bool o = ((f >> e) & 1) || (tp.mapX && tp.mapX[(int64_t)i * nb + j] >= 0);
             out_flag[(int64_t)i * nb + j] = o;
             if (mirror) out_flag[(int64_t)j * nb + i] = o;
             work |= o;
         }
-    }
-    if (b < rs.size()) {
-        cnt[b] = work ? c : 0;
+        const int64_t b = rs.index(I, J);
+        cnt[b] = work ? tcnt[J] : 0;
         wflag[b] = work;
     }
     for (int o = 16; o > 0; o >>= 1) {
         cand += __shfl_xor_sync(0xffffffffu, cand, o);
         kept += __shfl_xor_sync(0xffffffffu, kept, o);
     }
-    if ((threadIdx.x & 31) == 0 && cand) {
+    if ((t & 31) == 0 && cand) {
         atomicAdd(counters, cand);
         atomicAdd(counters + 1, kept);
     }
 }
 
-// per tile with outputs: work item, output slots, tasks; counters[0] formed products,
-// counters[1] (p, q) slice pairs issued over all passes
-__global__ void k_tile_fill(TilePlan tp, Raster rs, const int32_t* __restrict__ out_flag,
-                            const int64_t* __restrict__ out_idx, const double* __restrict__ d_tau,
-                            const int32_t* __restrict__ wflag, const int64_t* __restrict__ widx,
-                            const int64_t* __restrict__ toff, int32_t* __restrict__ work_ij,
-                            int32_t* __restrict__ work_out, int64_t* __restrict__ work_off,
-                            int32_t* __restrict__ task, unsigned long long* __restrict__ counters) {
-    const int nb = tp.nb;
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long formed = 0, pairs = 0;
-    int I = 0, J = 0;
-    if (b < rs.size() && wflag[b] && rs.unswizzle(b, &I, &J)) {
-        const int i0 = 2 * I, j0 = 2 * J;
+// per tile with outputs: work item, output slots, tasks in increasing k (one k at a
+// time over the CTA; the J of one k are distinct, so a per-J cursor places them);
+// counters[0] formed products, counters[1] (p, q) slice pairs issued over all passes
+__global__ void __launch_bounds__(256)
+k_tile_rows_fill(TilePlan tp, Raster rs, const int64_t* __restrict__ ptrA,
+                 const int32_t* __restrict__ idxA, const int64_t* __restrict__ ptrK,
+                 const int32_t* __restrict__ idxK, const int32_t* __restrict__ out_flag,
+                 const int64_t* __restrict__ out_idx, const double* __restrict__ d_tau,
+                 const int32_t* __restrict__ wflag, const int64_t* __restrict__ widx,
+                 const int64_t* __restrict__ toff, int32_t* __restrict__ work_ij,
+                 int32_t* __restrict__ work_out, int64_t* __restrict__ work_off,
+                 int32_t* __restrict__ task, unsigned long long* __restrict__ counters) {
+    extern __shared__ int32_t cursor[];   // [np]
+    const int np = rs.np, nb = tp.nb;
+    const int I = blockIdx.x, t = threadIdx.x;
+    const int i0 = 2 * I;
+    for (int J = t; J < np; J += blockDim.x) {
+        cursor[J] = 0;
+        if (tp.sym && J < I) continue;
+        const int64_t b = rs.index(I, J);
+        if (!wflag[b]) continue;
+        const int j0 = 2 * J;
         const int64_t w = widx[b];
-        work_ij[w] = I * rs.np + J;
+        work_ij[w] = I * np + J;
         const bool mirror = tp.sym && I < J;
         int32_t* wo = work_out + 8 * w;   // [2h + c] direct, [4 + 2h + c] transposed copy
-        for (int q = 0; q < 4; ++q) {
-            const int i = i0 + (q >> 1), j = j0 + (q & 1);
+        for (int e = 0; e < 4; ++e) {
+            const int i = i0 + (e >> 1), j = j0 + (e & 1);
             const bool in = i < nb && j < nb;
-            wo[q] = (in && out_flag[(int64_t)i * nb + j]) ? (int32_t)out_idx[(int64_t)i * nb + j] : -1;
-            wo[4 + q] = (in && mirror && out_flag[(int64_t)j * nb + i])
+            wo[e] = (in && out_flag[(int64_t)i * nb + j]) ? (int32_t)out_idx[(int64_t)i * nb + j] : -1;
+            wo[4 + e] = (in && mirror && out_flag[(int64_t)j * nb + i])
                             ? (int32_t)out_idx[(int64_t)j * nb + i]
                             : -1;
         }
-        int64_t t = toff[b];
-        work_off[w] = t;
-        const double tau = *d_tau;
-        for (int k = 0; k < nb; ++k) {
-            const double a0 = nrm(tp.nA, nb, i0, k), a1 = nrm(tp.nA, nb, i0 + 1, k);
+        work_off[w] = toff[b];
+    }
+    __syncthreads();
+    const double tau = *d_tau;
+    unsigned long long formed = 0, pairs = 0;
+    const int64_t qa1 = ptrA[I + 1];
+    for (int64_t q = ptrA[I]; q < qa1; ++q) {
+        const int k = idxA[q];
+        const double a0 = nrm(tp.nA, nb, i0, k), a1 = nrm(tp.nA, nb, i0 + 1, k);
+        const double ra = fmax(a0, a1);
+        const int32_t s0 = tp.mapA[(int64_t)i0 * nb + k];
+        const int32_t s1 = i0 + 1 < nb ? tp.mapA[(int64_t)(i0 + 1) * nb + k] : -1;
+        const int pa = min(s0 >= 0 ? (int)tp.p0A[s0] : MX_S + 1, s1 >= 0 ? (int)tp.p0A[s1] : MX_S + 1);
+        const int32_t pidA = (int32_t)tp.pidxA[(int64_t)I * nb + k];
+        const int64_t r1 = ptrK[k + 1];
+        for (int64_t r = ptrK[k] + t; r < r1; r += blockDim.x) {
+            const int J = idxK[r];
+            if (tp.sym && J < I) continue;
+            const int j0 = 2 * J;
             const double b0 = nrm(tp.nB, nb, k, j0), b1 = nrm(tp.nB, nb, k, j0 + 1);
-            const double m = fmax(a0, a1) * fmax(b0, b1);
+            const double m = ra * fmax(b0, b1);
             if (!(m > 0.0 && m >= tau)) continue;
-            const int32_t s0 = tp.mapA[(int64_t)i0 * nb + k];
-            const int32_t s1 = i0 + 1 < nb ? tp.mapA[(int64_t)(i0 + 1) * nb + k] : -1;
             const int32_t t0 = b_slot(tp, k, j0), t1 = b_slot(tp, k, j0 + 1);
-            const int pa = min(s0 >= 0 ? (int)tp.p0A[s0] : MX_S + 1, s1 >= 0 ? (int)tp.p0A[s1] : MX_S + 1);
             const int qb = min(t0 >= 0 ? (int)tp.p0B[t0] : MX_S + 1, t1 >= 0 ? (int)tp.p0B[t1] : MX_S + 1);
-            task[3 * t + 0] = (int32_t)tp.pidxA[(int64_t)I * nb + k];
-            task[3 * t + 1] = (int32_t)tp.pidxB[(int64_t)J * nb + k];
-            task[3 * t + 2] = pa | (qb << 8);
+            const int64_t at = toff[rs.index(I, J)] + cursor[J]++;
+            task[3 * at + 0] = pidA;
+            task[3 * at + 1] = (int32_t)tp.pidxB[(int64_t)J * nb + k];
+            task[3 * at + 2] = pa | (qb << 8);
             formed += (a0 * b0 > 0.0) + (a0 * b1 > 0.0) + (a1 * b0 > 0.0) + (a1 * b1 > 0.0);
             pairs += n_level_pairs(pa, qb, tp.lmax);
-            ++t;
         }
+        __syncthreads();
     }
     for (int o = 16; o > 0; o >>= 1) {
         formed += __shfl_xor_sync(0xffffffffu, formed, o);
         pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
     }
-    if ((threadIdx.x & 31) == 0 && formed) {
+    if ((t & 31) == 0 && formed) {
         atomicAdd(counters, formed);
         atomicAdd(counters + 1, pairs);
     }
@@ -920,6 +985,23 @@ static int set_pass_attributes(spamm_ctx* ctx) {
 
 int mixed_available() { return 1; }
 
+// The tile planners keep one or two int32 per pair column in shared memory.
+constexpr size_t TILE_PLAN_SMEM_MAX = 200 * 1024;
+
+static int tile_plan_attributes(size_t smem) {
+    if (smem > TILE_PLAN_SMEM_MAX) {
+        set_error("mixed planner: the pair grid is too wide for its shared-memory row buffer");
+        return SPAMM_ENOTSUP;
+    }
+    if (smem > 48 * 1024) {
+        SP_CUDA(cudaFuncSetAttribute(k_tile_rows_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TILE_PLAN_SMEM_MAX));
+        SP_CUDA(cudaFuncSetAttribute(k_tile_rows_fill, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TILE_PLAN_SMEM_MAX));
+    }
+    return SPAMM_OK;
+}
+
 int mixed_prepare(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, int sym,
                   MixedPrep* mp) {
     if (A->bs != MX_BS) {
@@ -1012,10 +1094,21 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     SP_TRY(dalloc((void**)&oidx, sizeof(int64_t) * (nb2 + 1), s));
     SP_TRY(dalloc((void**)&d_tot, 16, s));
     SP_CUDA(cudaMemsetAsync(of, 0, sizeof(int32_t) * nb2, s));
+    SP_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * ntile, s));
+    SP_CUDA(cudaMemsetAsync(wf, 0, sizeof(int32_t) * ntile, s));
     SP_CUDA(cudaMemsetAsync(&sc->n_cand, 0, 2 * sizeof(unsigned long long), s));
-    const unsigned G = (unsigned)((ntile + 255) / 256);
+    // pair rows of A (the k of every I) and, for every k, the J of the B operand's pair
+    // tiles (J, k)
+    BlockLists prA, pkB;
+    SP_TRY(lists_build_i64(ctx, sa->pair_idx, np, nb, 0, &prA));
+    SP_TRY(lists_build_i64(ctx, sbs->pair_idx, np, nb, 1, &pkB));
+    const size_t smem_count = sizeof(int32_t) * 2 * (size_t)np;
+    const size_t smem_fill = sizeof(int32_t) * (size_t)np;
+    SP_TRY(tile_plan_attributes(smem_count));
+    const unsigned G = (unsigned)(np > 0 ? np : 1);
     ++ctx->launches;
-    k_tile_count<<<G, 256, 0, s>>>(tp, rs, d_tau, cnt, wf, of, &sc->n_cand);
+    k_tile_rows_count<<<G, 256, smem_count, s>>>(tp, rs, prA.d_ptr, prA.d_idx, pkB.d_ptr,
+                                                 pkB.d_idx, d_tau, cnt, wf, of, &sc->n_cand);
     SP_CHECK_LAUNCH();
     SP_TRY(scan_i32_to_i64(ctx, of, oidx, nb2, &sc->n_out));
     SP_TRY(scan_i32_to_i64(ctx, cnt, toff, ntile, d_tot));
@@ -1043,8 +1136,9 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     SP_TRY(dalloc((void**)&parts, sizeof(double) * 12 * nw, s));
     SP_CUDA(cudaMemsetAsync(&sc->mx_formed, 0, 2 * sizeof(unsigned long long), s));
     ++ctx->launches;
-    k_tile_fill<<<G, 256, 0, s>>>(tp, rs, of, oidx, d_tau, wf, widx, toff, work_ij, work_out,
-                                  work_off, task, &sc->mx_formed);
+    k_tile_rows_fill<<<G, 256, smem_fill, s>>>(tp, rs, prA.d_ptr, prA.d_idx, pkB.d_ptr, pkB.d_idx,
+                                               of, oidx, d_tau, wf, widx, toff, work_ij, work_out,
+                                               work_off, task, &sc->mx_formed);
     ++ctx->launches;
     k_last_off<<<1, 1, 0, s>>>(work_off, n_work, toff, ntile);
     SP_CHECK_LAUNCH();
@@ -1120,6 +1214,8 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
         SP_CUDA(cudaMemsetAsync(&sc->fro2, 0, 3 * sizeof(double), s));
         cudaEventRecord(ctx->ev[EV_GEMM1], s);
     }
+    prA.free(s);
+    pkB.free(s);
     dfree(cnt, s); dfree(wf, s); dfree(of, s); dfree(toff, s); dfree(widx, s); dfree(oidx, s);
     dfree(d_tot, s);
     dfree(work_ij, s); dfree(work_out, s); dfree(work_off, s); dfree(task, s); dfree(parts, s);

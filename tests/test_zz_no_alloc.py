@@ -33,7 +33,8 @@ def test_noalloc_search_matches_spamm_multiply_twice():
     # entry of the scratch's first level buffer and it folds one level more
     cases = [(synth.banded_decay(1000, 31, length=40.0), 64, 1e-6),
              (synth.random_decaying(700, 32, length=30.0), 32, 1e-4),
-             (synth.banded_decay(6400, 33, length=40.0), 32, 1e-6)]
+             (synth.banded_decay(6400, 33, length=40.0), 32, 1e-6),
+             (synth.lattice_fock_blocks(2048, seed=34, bs=32, cutoff=1.5).to_dense(), 32, 1e-6)]
     for X, bs, delta in cases:
         G = ctx.from_dense(X, bs)
         _, rep = ctx.multiply(G, G, delta, prec="fp64")
