@@ -272,12 +272,26 @@ class PurifyResult:
     taus: list
     traces: list
     idem: list
+    # propagated eigenvalue bounds of the iterate: entry 0 for X_0 (after its
+    # truncation), entry i after accepted step i; the unoccupied eigenvalues of
+    # X_i are <= hs[i] and the occupied ones >= ls[i]
+    hs: list = dataclasses.field(default_factory=list)
+    ls: list = dataclasses.field(default_factory=list)
+    iterates: list = None        # X_0, X_1, ... when asked for
 
 
 def purify(F, n_occ: int, eps: float, n_iter: int, homo: float, lumo: float,
-           variant: int = 5, bs: int = 64, lmin=None, lmax=None) -> PurifyResult:
+           variant: int = 5, bs: int = 64, lmin=None, lmax=None, keep_iterates: bool = False,
+           perturb=None) -> PurifyResult:
     """SP2 purification with error control: Algorithm 1 (variant=1, truncmul),
-    Algorithm 4 (variant=4, SpAMM only) or Algorithm 5 (variant=5, hybrid)."""
+    Algorithm 4 (variant=4, SpAMM only) or Algorithm 5 (variant=5, hybrid).
+
+    keep_iterates: also return every iterate X_0, X_1, ... (res.iterates).
+    perturb: a test hook, callable (X, delta) -> E with ||E||_F <= delta. When given,
+    every step's error (Algorithm 1's E_i, and X_0's truncation) is E instead of
+    what truncation or SpAMM would make: the products are exact and E is added,
+    so a test can put the largest error the step tolerance allows where it does
+    the most harm."""
     F = _f64(F)
     n = F.shape[0]
     if n_occ in (0, n):
@@ -294,8 +308,12 @@ def purify(F, n_occ: int, eps: float, n_iter: int, homo: float, lumo: float,
     res = PurifyResult(None, 0, False, [], [], [], [], [])
     if variant in (1, 5):
         d0 = budget * (l - h)
-        X = truncate(X, d0, bs).X
+        X = X + perturb(X, d0) if perturb else truncate(X, d0, bs).X
         h, l = h + d0, l - d0
+    res.hs.append(h)
+    res.ls.append(l)
+    if keep_iterates:
+        res.iterates = [X]
     for it in range(1, n_iter + 1):
         tr = float(np.trace(X))
         sq = tr > n_occ
@@ -304,7 +322,7 @@ def purify(F, n_occ: int, eps: float, n_iter: int, homo: float, lumo: float,
         else:
             hn, ln = 2 * h - h * h, 2 * l - l * l
         delta = budget * (ln - hn)
-        if variant == 1:
+        if variant == 1 or perturb:
             C = X @ X
             bound, tau = 0.0, 0.0
         else:
@@ -317,7 +335,9 @@ def purify(F, n_occ: int, eps: float, n_iter: int, homo: float, lumo: float,
             res.converged = True
             break
         Xn = C if sq else 2.0 * X - C
-        if variant == 1:
+        if perturb:
+            Xn = Xn + perturb(Xn, delta)
+        elif variant == 1:
             Xn = truncate(Xn, delta, bs).X
         elif variant == 5:
             Xn = truncate(Xn, 0.5 * delta, bs).X
@@ -326,6 +346,10 @@ def purify(F, n_occ: int, eps: float, n_iter: int, homo: float, lumo: float,
         res.deltas.append(delta)
         res.taus.append(tau)
         res.iters = it
+        res.hs.append(h)
+        res.ls.append(l)
+        if keep_iterates:
+            res.iterates.append(Xn)
         X = Xn
     res.D = X
     return res
