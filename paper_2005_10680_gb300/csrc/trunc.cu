@@ -9,8 +9,9 @@
 //
 // GPU form, with no sort: only units with weight < delta^2 can be removed.
 // Their weights become integer keys ceil(w / delta^2 * 2^62) (rounded up, so
-// a key sum below 2^62 certifies a weight sum below delta^2). One CTA then
-// runs an 8-pass most-significant-digit radix select on the keys: each pass
+// a key sum below 2^62 certifies a weight sum below delta^2), and a scan packs
+// these candidate units in block order. One CTA then runs an 8-pass
+// most-significant-digit radix select on the packed keys: each pass
 // histograms (count, 128-bit exact sum) of the keys that share the digits
 // fixed so far, and walks the 256 buckets in order to find the bucket where
 // the running sum reaches 2^62. After 8 passes the boundary key K* is exact:
@@ -27,7 +28,7 @@ constexpr unsigned long long KEY_ONE = 1ull << 62;   // delta^2 in key units
 
 __global__ void k_trunc_keys(const int32_t* __restrict__ map, const double* __restrict__ norm,
                              int nb, int symmetric, double delta2,
-                             unsigned long long* __restrict__ keys) {
+                             unsigned long long* __restrict__ keys, int32_t* __restrict__ cand) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nb2 = (int64_t)nb * nb;
     if (b >= nb2) return;
@@ -52,6 +53,19 @@ __global__ void k_trunc_keys(const int32_t* __restrict__ map, const double* __re
         if (w == 0.0) key = 0;
     }
     keys[b] = key;
+    cand[b] = key != NOT_CAND;
+}
+
+// the candidate units in block order (the exclusive scan of the candidate flags
+// gives each one its place)
+__global__ void k_trunc_compact(const unsigned long long* __restrict__ keys,
+                                const int32_t* __restrict__ cand, const int64_t* __restrict__ pos,
+                                int64_t nb2, unsigned long long* __restrict__ keys_c,
+                                int64_t* __restrict__ unit_c) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb2 || !cand[b]) return;
+    keys_c[pos[b]] = keys[b];
+    unit_c[pos[b]] = b;
 }
 
 struct U128 {
@@ -72,9 +86,12 @@ __device__ __forceinline__ bool below_one(const U128& a) { return a.hi == 0 && a
 
 // Single CTA (1024 threads): radix select, then mark removals.
 __global__ void __launch_bounds__(1024)
-k_trunc_select(const unsigned long long* __restrict__ keys, int64_t nb2, int nb, int symmetric,
+k_trunc_select(const unsigned long long* __restrict__ keys, const int64_t* __restrict__ unit,
+               const unsigned long long* __restrict__ d_count, int nb, int symmetric,
                int32_t* __restrict__ map, double* __restrict__ norm, int32_t* __restrict__ coord,
                DevScalars* sc) {
+    // keys[0 .. count) are the candidate units in block order, unit[] their block index
+    const int64_t nb2 = (int64_t)*d_count;
     __shared__ unsigned long long h_cnt[256];
     __shared__ unsigned long long h_lo[256];
     __shared__ unsigned long long h_hi[256];
@@ -193,12 +210,13 @@ k_trunc_select(const unsigned long long* __restrict__ keys, int64_t nb2, int nb,
         }
         if (rem) {
             add128(rsum, k);
-            const int i = (int)(b / nb), j = (int)(b % nb);
-            const int32_t s0 = map[b];
+            const int64_t ub = unit[b];
+            const int i = (int)(ub / nb), j = (int)(ub % nb);
+            const int32_t s0 = map[ub];
             if (s0 >= 0) {
                 coord[s0] = -1;
-                map[b] = -1;
-                norm[b] = 0.0;
+                map[ub] = -1;
+                norm[ub] = 0.0;
                 ++removed;
             }
             if (symmetric && i != j) {
@@ -251,15 +269,27 @@ int truncate_blocks(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric, i
     DevScalars* sc = (DevScalars*)ctx->d_scalars;
     const int nb = X->nb;
     const int64_t nb2 = (int64_t)nb * nb;
-    unsigned long long* keys = nullptr;
+    unsigned long long *keys = nullptr, *keys_c = nullptr, *d_count = nullptr;
+    int32_t* cand = nullptr;
+    int64_t *pos = nullptr, *unit_c = nullptr;
     SP_TRY(dalloc((void**)&keys, sizeof(unsigned long long) * nb2, s));
+    SP_TRY(dalloc((void**)&cand, sizeof(int32_t) * nb2, s));
+    SP_TRY(dalloc((void**)&pos, sizeof(int64_t) * (nb2 + 1), s));
+    SP_TRY(dalloc((void**)&keys_c, sizeof(unsigned long long) * nb2, s));
+    SP_TRY(dalloc((void**)&unit_c, sizeof(int64_t) * nb2, s));
+    SP_TRY(dalloc((void**)&d_count, sizeof(unsigned long long), s));
     const double delta2 = delta * delta;
+    const unsigned G = (unsigned)((nb2 + 255) / 256);
     ++ctx->launches;
-    k_trunc_keys<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(X->d_map, X->d_norm, nb, symmetric,
-                                                               delta2, keys);
+    k_trunc_keys<<<G, 256, 0, s>>>(X->d_map, X->d_norm, nb, symmetric, delta2, keys, cand);
+    SP_CHECK_LAUNCH();
+    // only units lighter than delta^2 can be removed: the select runs over those alone
+    SP_TRY(scan_i32_to_i64(ctx, cand, pos, nb2, d_count));
     ++ctx->launches;
-    k_trunc_select<<<1, 1024, 0, s>>>(keys, nb2, nb, symmetric, X->d_map, X->d_norm, X->d_coord,
-                                      sc);
+    k_trunc_compact<<<G, 256, 0, s>>>(keys, cand, pos, nb2, keys_c, unit_c);
+    ++ctx->launches;
+    k_trunc_select<<<1, 1024, 0, s>>>(keys_c, unit_c, d_count, nb, symmetric, X->d_map, X->d_norm,
+                                      X->d_coord, sc);
     SP_CUDA(cudaMemsetAsync(&sc->n_out, 0, sizeof(unsigned long long), s));
     ++ctx->launches;
     k_count_live<<<64, 256, 0, s>>>(X->d_map, nb2, &sc->n_out);
@@ -271,6 +301,11 @@ int truncate_blocks(spamm_ctx* ctx, spamm_mat* X, double delta, int symmetric, i
     SP_CUDA(cudaMemcpyAsync(&h_live, &sc->n_out, 8, cudaMemcpyDeviceToHost, s));
     SP_CUDA(cudaStreamSynchronize(s));
     dfree(keys, s);
+    dfree(cand, s);
+    dfree(pos, s);
+    dfree(keys_c, s);
+    dfree(unit_c, s);
+    dfree(d_count, s);
     X->nnzb = (int64_t)h_live;
     if (removed) *removed = (int64_t)h_rem;
     if (removed_sq) *removed_sq = h_sq * delta2;
