@@ -200,16 +200,26 @@ class Matrix:
                "spamm_mat_to_dense")
         return out
 
-    def to_blocks(self):
+    def to_blocks(self, out=None):
         """The stored leaf blocks, row-major: (brow, bcol, tiles) with tiles of shape
-        (nnzb, bs, bs) (the inverse of Context.from_blocks)."""
+        (nnzb, bs, bs) (the inverse of Context.from_blocks). `out` (optional): a host
+        buffer (numpy array or CPU torch tensor, ideally pinned) of at least
+        nnzb * bs * bs float64 to write the tiles into; the returned tiles then view it."""
         n, bs, nnzb = self.info()
         brow = np.empty(nnzb, dtype=np.int32)
         bcol = np.empty(nnzb, dtype=np.int32)
-        tiles = np.empty((nnzb, bs, bs))
+        if out is None:
+            tiles = np.empty((nnzb, bs, bs))
+            ptr = tiles.ctypes.data
+        else:
+            size = out.numel() if _is_torch(out) else out.size
+            if size < nnzb * bs * bs:
+                raise ValueError(f"to_blocks: buffer of {size} entries, {nnzb * bs * bs} needed")
+            ptr = out.data_ptr() if _is_torch(out) else out.ctypes.data
+            tiles = (out.reshape(-1)[: nnzb * bs * bs].reshape(nnzb, bs, bs))
         _check(_lib.spamm_mat_to_blocks(self.ctx.handle, self.handle,
                                         brow.ctypes.data_as(_PI32), bcol.ctypes.data_as(_PI32),
-                                        tiles.ctypes.data, 0), "spamm_mat_to_blocks")
+                                        ptr, 0), "spamm_mat_to_blocks")
         return brow, bcol, tiles
 
     def get_blocks(self, brow, bcol):

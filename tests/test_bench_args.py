@@ -10,7 +10,7 @@ import bench
 def test_defaults_are_the_papers():
     args = bench.parse([])
     assert args.bound == "alg3" and bench.tau_table_config(args) is None
-    assert args.n == 16384 and args.bs == 64 and args.eps == 1e-5
+    assert args.n == 262144 and args.bs == 64 and args.eps == 1e-5 and args.spamm_delta == 1e-7
 
 
 def test_spectral_bound_only_with_the_protocol():
@@ -35,14 +35,16 @@ def test_reference_arm_line_on_a_small_case():
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    flags = ["--n", "4096", "--sample-n", "1024", "--cores", "2", "--steps", "1", "--warmup", "0"]
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                          "--n", "512", "--sample-n", "256", "--steps", "1", "--warmup", "0"],
-                         capture_output=True, text=True, timeout=600)
+                          *flags], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["unit"] == "ms" and line["higher_is_better"] is False and line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 2
+    # the same config as the GPU arm's line for the same flags
+    assert line["config"] == bench.config_of(bench.parse(flags))
     assert line["cpu_baseline"]["value"] == line["value"] and line["cpu_baseline"]["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "ms", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
