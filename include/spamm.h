@@ -117,6 +117,13 @@ void spamm_destroy(spamm_ctx* ctx);
 const char* spamm_strerror(int status);
 const char* spamm_last_error(void);
 
+/* Test hook for the failure paths (the paper has no counterpart): the library's
+   device allocation that follows `after` more successful ones fails with
+   SPAMM_ENOMEM, once; after < 0 disarms it. Every entry point must then return that
+   status and leave its context usable for the next call. Process-wide (all contexts
+   and threads share one counter). Returns SPAMM_OK. */
+int spamm_debug_fail_alloc(int64_t after);
+
 /* Number of CUDA kernels this context has launched so far (a profiling counter:
    every kernel launch site of the library increments it on the host). */
 int64_t spamm_ctx_launches(const spamm_ctx* ctx);

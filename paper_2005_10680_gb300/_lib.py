@@ -113,6 +113,7 @@ def load_library(build_if_stale: bool = True):
         "spamm_cse_search_noalloc": ([vp, vp, i64, d, vp, vp, vp, vp], i32),
         "spamm_autotune": ([vp, vp, d, i32, P(TuneResult)], i32),
         "spamm_set_bound": ([vp, i32], i32),
+        "spamm_debug_fail_alloc": ([i64], i32),
         "spamm_set_tau_table": ([vp, d, d], i32),
         "spamm_purify_batched": ([vp, i32, P(vp), P(i64), d, i32, P(PurifyOpts), i32, P(vp),
                                   P(PurifyReport), P(ctypes.c_int32)], i32),

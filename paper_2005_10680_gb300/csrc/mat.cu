@@ -7,6 +7,7 @@
 // nb x nb float64 map of leaf Frobenius norms (0 for absent blocks). The
 // quadtree of Eq. 2 is implicit: the level-l node of block (i, j) is
 // (i >> l, j >> l) on the padded grid of 2^L >= nb blocks.
+#include <atomic>
 #include <cstdarg>
 #include <cstring>
 
@@ -32,8 +33,16 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return e == cudaErrorMemoryAllocation ? SPAMM_ENOMEM : SPAMM_ECUDA;
 }
 
+// Allocation-failure injection for the failure-path tests: while the counter is
+// k >= 0, the allocation after k more successful ones fails (once).
+static std::atomic<long long> g_fail_after{-1};
+
 int dalloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
+    if (g_fail_after.load(std::memory_order_relaxed) >= 0 && g_fail_after.fetch_sub(1) == 0) {
+        set_error("device allocation of %zu bytes refused (injected failure)", bytes);
+        return SPAMM_ENOMEM;
+    }
     if (bytes == 0) bytes = 16;
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -380,6 +389,11 @@ int reduce_partials(spamm_ctx* ctx, const double* d_fro2, const double* d_trace,
 using namespace spamm;
 
 extern "C" const char* spamm_last_error(void) { return spamm::last_error(); }
+
+extern "C" int spamm_debug_fail_alloc(int64_t after) {
+    spamm::g_fail_after.store(after >= 0 ? (long long)after : -1);
+    return SPAMM_OK;
+}
 
 extern "C" int spamm_mat_from_dense(spamm_ctx* ctx, const double* a, int64_t n, int64_t ld,
                                     int bs, double drop_abs, int a_on_device, spamm_mat** out) {

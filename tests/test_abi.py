@@ -111,6 +111,7 @@ def test_entry_points_reject_null_handles_without_a_gpu():
     assert lib.spamm_ctx_launches(null) == 0
     lib.spamm_destroy(null)
     lib.spamm_mat_free(null)
+    assert lib.spamm_debug_fail_alloc(-1) == 0          # the test hook needs no GPU either
 
 
 def test_header_is_c_and_the_library_links_from_c(tmp_path):
