@@ -318,31 +318,47 @@ __global__ void k_zero_rows(double* out, int64_t n, int64_t ld) {
     for (int64_t c = threadIdx.x; c < n; c += blockDim.x) out[r * ld + c] = 0.0;
 }
 
-// Sum of the diagonal of diagonal blocks, in block order (one CTA, fixed order).
-__global__ void k_trace(const double* __restrict__ tiles, const int32_t* __restrict__ map, int nb,
-                        int bs, double* __restrict__ out) {
-    __shared__ double sh[1024];
+// Trace: one warp per diagonal block sums its diagonal (a fixed order per lane and
+// a fixed shuffle tree), then one CTA sums the nb partials in a fixed order.
+__global__ void k_trace_blocks(const double* __restrict__ tiles, const int32_t* __restrict__ map,
+                               int nb, int bs, double* __restrict__ part) {
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= nb) return;
+    const int32_t s = map[i * nb + i];
     double acc = 0.0;
-    for (int i = 0; i < nb; ++i) {
-        int32_t s = map[(int64_t)i * nb + i];
-        double v = 0.0;
-        if (s >= 0 && (int)threadIdx.x < bs) v = tiles[(int64_t)s * bs * bs + threadIdx.x * (bs + 1)];
-        sh[threadIdx.x] = v;
-        __syncthreads();
-        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) acc += sh[0];
+    if (s >= 0)
+        for (int r = lane; r < bs; r += 32) acc += tiles[(int64_t)s * bs * bs + (int64_t)r * (bs + 1)];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) part[i] = acc;
+}
+
+__global__ void __launch_bounds__(1024) k_sum_fixed(const double* __restrict__ part, int count,
+                                                    double* __restrict__ out) {
+    __shared__ double sh[1024];
+    const int t = threadIdx.x;
+    double v = 0.0;
+    for (int i = t; i < count; i += 1024) v += part[i];
+    sh[t] = v;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (t < o) sh[t] += sh[t + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *out = acc;
+    if (t == 0) *out = sh[0];
 }
 
 int mat_trace(spamm_ctx* ctx, const spamm_mat* X, double* d_out) {
-    ++ctx->launches;
-    k_trace<<<1, 128, 0, ctx->stream>>>(X->d_tiles, X->d_map, X->nb, X->bs, d_out);
+    cudaStream_t s = ctx->stream;
+    double* part = nullptr;
+    SP_TRY(dalloc((void**)&part, sizeof(double) * (X->nb > 0 ? X->nb : 1), s));
+    ctx->launches += 2;
+    k_trace_blocks<<<(unsigned)(((int64_t)X->nb * 32 + 255) / 256), 256, 0, s>>>(
+        X->d_tiles, X->d_map, X->nb, X->bs, part);
+    k_sum_fixed<<<1, 1024, 0, s>>>(part, X->nb, d_out);
     SP_CHECK_LAUNCH();
+    dfree(part, s);
     return SPAMM_OK;
 }
 

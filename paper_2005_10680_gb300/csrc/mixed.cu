@@ -64,11 +64,17 @@ __global__ void k_block_rowmax(const double* __restrict__ tiles, const int32_t* 
     }
     double m = 0.0;
     if (!transpose) {
-        const int row = t >> 2, q = t & 3;
-        for (int c = q * 16; c < q * 16 + 16; ++c) m = fmax(m, fabs(T[row * MX_BS + c]));
-        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
-        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
-        if (q == 0) rmax[s * 64 + row] = m;
+        // warp w takes half rows w, w + 8, ...: 32 consecutive entries per load
+        const int w = t >> 5, lane = t & 31;
+        double* hm = &sh[0][0];                  // [128] half-row maxima
+        for (int hr = w; hr < 2 * MX_BS; hr += 8) {
+            double v = fabs(T[(hr >> 1) * MX_BS + (hr & 1) * 32 + lane]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+            if (lane == 0) hm[hr] = v;
+        }
+        __syncthreads();
+        if (t < 64) rmax[s * 64 + t] = fmax(hm[2 * t], hm[2 * t + 1]);
     } else {
         const int col = t & 63, q = t >> 6;
         for (int r = q * 16; r < q * 16 + 16; ++r) m = fmax(m, fabs(T[r * MX_BS + col]));
@@ -100,14 +106,31 @@ __global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __re
 // One CTA (256 threads) per stored block: digits, leading-zero slice, slice and
 // tail norms, in integer arithmetic. With |x| < 2^e_r, V = x 2^(63 - e_r) is
 // rounded to an int64 (the rounding is the last tail, at most half a unit) and
-// cut from the bottom into balanced base-128 digits:
-//     d = ((V + 64) mod 128) - 64 in [-64, 63], V <- (V - d) / 128, ..., d_1 = V,
-// so x = sum_p d_p 2^(e_r - 7p) + T_9 with |d_1| <= 128, |T_9| <= 2^(e_r - 64).
-// Slice norms are exact (digit squares summed exactly per row in f32); tail norms
-// are upper bounds: |R_p| per entry, plus 1/2 where the rounding of V was inexact,
-// summed in f32 and inflated by 2^-12 to cover the f32 rounding. transpose: slice the
-// transposed block with column exponents. The digits go to the block's half of its
-// pair tile.
+// cut into balanced base-128 digits,
+//     V = d_1 2^56 + sum_{p=2..9} d_p 2^(7 (9 - p)),  d_p in [-64, 63] for p >= 2,
+// so x = sum_p d_p 2^(e_r - 7p) + T_9 with |d_1| <= 128, |T_9| <= 2^(e_r - 64). The
+// digits are read off V + C, C = 64 sum_{q<8} 128^q: its low 56 bits hold the
+// digits d_p + 64 (p >= 2) in plain base 128, so every digit (and every tail
+// R_p = sum_{q>p} d_q 2^(7 (9 - q)) = (low 7 (9 - p) bits) - C_p) is computed
+// independently of the others. Slice norms are exact (digit squares summed exactly
+// per row in f32); tail norms are upper bounds: |R_p| per entry, plus 1/2 where the
+// rounding of V was inexact, summed in f32 and inflated by 2^-12 to cover the f32
+// rounding. transpose: slice the transposed block with column exponents. The digits
+// go to the block's half of its pair tile.
+constexpr unsigned long long M56 = (1ull << 56) - 1;
+
+__host__ __device__ constexpr unsigned long long digit_offset(int low_digits) {
+    // 64 * (128^low_digits - 1) / 127: the offset that makes low_digits balanced
+    // base-128 digits non-negative
+    return 64ull * (((1ull << (7 * low_digits)) - 1ull) / 127ull);
+}
+
+__device__ __forceinline__ double pow2_exact(int e) {
+    // 2^e; a constructed power of two where it is a normal double
+    return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
+                                     : ldexp(1.0, e);
+}
+
 __global__ void __launch_bounds__(256, 3)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
         const int32_t* __restrict__ expo, uint8_t* __restrict__ pairs,
@@ -116,7 +139,8 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
     const int64_t s = blockIdx.x;
     const int t = threadIdx.x;
     __shared__ double T[MX_BS][MX_BS + 1];
-    __shared__ double red_a[8][MX_S], red_r[8][MX_S];
+    __shared__ float row_a[MX_BS][MX_S], row_r[MX_BS][MX_S];   // per-row sums
+    __shared__ int row_e[MX_BS];
     __shared__ int first;
     const int32_t cd = coord[s];
     if (t == 0) first = MX_S + 1;
@@ -132,7 +156,7 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
     const int base = (transpose ? bj : bi) * MX_BS;
     const int row = t >> 2, kq = t & 3;           // kq: two groups of 8 K values each
     const int e_r = expo[base + row];
-    float sa[MX_S], sr[MX_S];                     // per-row sums of d_p^2 and (|R_p| + 1/2)^2
+    float sa[MX_S], sr[MX_S];                     // per-thread sums of d_p^2 and (|R_p| + 1/2)^2
 #pragma unroll
     for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.f;
     int firstp = MX_S + 1;
@@ -173,16 +197,20 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             }
             if (bits < 0) V = -V;
             const float half = inexact ? 0.5f : 0.f;
-            long long rem = V;                     // digits from the bottom
+            // V = hi 2^56 + lo, lo in [0, 2^56); lo + C = carry 2^56 + L with L the digits + 64
+            const unsigned long long tt = ((unsigned long long)V & M56) + digit_offset(8);
+            const unsigned long long L = tt & M56;
+            const int d1 = (int)(V >> 56) + (int)(tt >> 56);
 #pragma unroll
-            for (int p = MX_S - 1; p >= 0; --p) {
-                const int d = p > 0 ? (int)(((rem + 64) & 127) - 64) : (int)rem;
-                if (p > 0) {
-                    rem = (rem - d) >> 7;
-                    // tail after digit p (in units of 2^(e_r - 63)): V - rem 2^(7(S - p))
-                    const long long Rp = V - rem * (1ll << (MX_W * (MX_S - p)));
+            for (int p = 0; p < MX_S; ++p) {       // slice p + 1
+                const int d = p == 0 ? d1 : (int)((L >> (MX_W * (MX_S - 1 - p))) & 127ull) - 64;
+                if (p < MX_S - 1) {
+                    // tail after digit p + 1 (in units of 2^(e_r - 63)): the digits below it
+                    const int low = MX_S - 1 - p;
+                    const long long Rp =
+                        (long long)(L & ((1ull << (MX_W * low)) - 1ull)) - (long long)digit_offset(low);
                     const float rf = fabsf((float)Rp) + half;
-                    sr[p - 1] = fmaf(rf, rf, sr[p - 1]);
+                    sr[p] = fmaf(rf, rf, sr[p]);
                 }
                 sa[p] = fmaf((float)d, (float)d, sa[p]);
                 if (d != 0 && p + 1 < firstp) firstp = p + 1;
@@ -198,30 +226,46 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
         }
     }
-    // per-row sums -> scale by 2^(2(e_r - 7p)) (slice) or 2^(2(e_r - 63)) (tail) -> block sums
+    // per-row sums over the row's 4 lanes, in f32: exact for the digit squares (integers
+    // below 2^24), covered by the 2^-12 inflation for the tails
 #pragma unroll
     for (int p = 0; p < MX_S; ++p) {
-        double a = (double)sa[p] * ldexp(1.0, 2 * (e_r - MX_W * (p + 1)));
-        double r = (double)sr[p] * (1.0 + ldexp(1.0, -12)) * ldexp(1.0, 2 * (e_r - MX_W * MX_S));
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            r += __shfl_xor_sync(0xffffffffu, r, o);
+        sa[p] += __shfl_xor_sync(0xffffffffu, sa[p], 1);
+        sa[p] += __shfl_xor_sync(0xffffffffu, sa[p], 2);
+        sr[p] += __shfl_xor_sync(0xffffffffu, sr[p], 1);
+        sr[p] += __shfl_xor_sync(0xffffffffu, sr[p], 2);
+    }
+    if (kq == 0) {
+#pragma unroll
+        for (int p = 0; p < MX_S; ++p) {
+            row_a[row][p] = sa[p];
+            row_r[row][p] = sr[p];
         }
-        if ((t & 31) == 0) {
-            red_a[t >> 5][p] = a;
-            red_r[t >> 5][p] = r;
-        }
+        row_e[row] = e_r;
     }
     atomicMin(&first, firstp);
     __syncthreads();
-    if (t < MX_S) {
-        double a = 0.0, r = 0.0;
-        for (int w = 0; w < 8; ++w) {
-            a += red_a[w][t];
-            r += red_r[w][t];
+    // rows scaled by 2^(2 (e_r - 7p)) (slice p) or 2^(2 (e_r - 63)) (tails) and summed in
+    // float64: warp 0 the slices, warp 1 the tails, two rows per lane
+    const int warp = t >> 5, lane = t & 31;
+    if (warp < 2) {
+        const int e0 = row_e[lane], e1 = row_e[lane + 32];
+#pragma unroll
+        for (int p = 0; p < MX_S; ++p) {
+            double v;
+            if (warp == 0)
+                v = (double)row_a[lane][p] * pow2_exact(2 * (e0 - MX_W * (p + 1))) +
+                    (double)row_a[lane + 32][p] * pow2_exact(2 * (e1 - MX_W * (p + 1)));
+            else
+                v = (double)row_r[lane][p] * pow2_exact(2 * (e0 - MX_W * MX_S)) +
+                    (double)row_r[lane + 32][p] * pow2_exact(2 * (e1 - MX_W * MX_S));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) {
+                if (warp == 0) sn[s * MX_S + p] = sqrt(v);
+                else tn[s * MX_S + p] = sqrt(v * (1.0 + 0x1p-12)) * (1.0 + 0x1p-40);
+            }
         }
-        sn[s * MX_S + t] = sqrt(a);
-        tn[s * MX_S + t] = sqrt(r) * (1.0 + ldexp(1.0, -40));
     }
     if (t == 0) p0[s] = (int8_t)first;
 }
@@ -267,22 +311,40 @@ __global__ void k_pair_index(const int32_t* __restrict__ flag, int64_t* __restri
     if (e < n && !flag[e]) idx[e] = -1;
 }
 
-// zero the half of every pair tile whose block is not stored (a CTA per (I, k) at a
-// time, over a grid-stride loop; absent pairs are passed over)
+// zero the half of every pair tile whose block is not stored: each warp checks 32
+// entries (I, k) at a time, then zeroes the missing halves among them together
 __global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb, int transpose,
                                     const int64_t* __restrict__ idx, int64_t ne,
                                     uint8_t* __restrict__ pairs) {
-    for (int64_t e = blockIdx.x; e < ne; e += gridDim.x) {
-        const int64_t pi = idx[e];
-        if (pi < 0) continue;
-        const int I = (int)(e / nb), k = (int)(e % nb);
-        for (int half = 0; half < 2; ++half) {
-            if (pair_block(map, nb, transpose, 2 * I + half, k) >= 0) continue;
-            uint8_t* base = pairs + pi * (int64_t)PAIR_BYTES + half * CHUNK;
-            for (int o = threadIdx.x; o < KCH * MX_S * (CHUNK / 16); o += blockDim.x) {
-                const int ch = o / (CHUNK / 16), w = o % (CHUNK / 16);   // ch: (K chunk, slice)
-                *reinterpret_cast<uint4*>(base + (int64_t)ch * 2 * CHUNK + w * 16) =
-                    make_uint4(0, 0, 0, 0);
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t base = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < ne;
+         base += warps * 32) {
+        const int64_t e = base + lane;
+        int64_t pi = -1;
+        int miss = 0;                             // bit h: half h is absent
+        if (e < ne) {
+            pi = idx[e];
+            if (pi >= 0) {
+                const int I = (int)(e / nb), k = (int)(e % nb);
+                for (int h = 0; h < 2; ++h)
+                    if (pair_block(map, nb, transpose, 2 * I + h, k) < 0) miss |= 1 << h;
+            }
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, miss != 0);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int64_t p = __shfl_sync(0xffffffffu, pi, src);
+            const int mm = __shfl_sync(0xffffffffu, miss, src);
+            for (int h = 0; h < 2; ++h) {
+                if (!((mm >> h) & 1)) continue;
+                uint8_t* hb = pairs + p * (int64_t)PAIR_BYTES + h * CHUNK;
+                for (int o = lane; o < KCH * MX_S * (CHUNK / 16); o += 32) {
+                    const int ch = o / (CHUNK / 16), w = o % (CHUNK / 16);   // (K chunk, slice)
+                    *reinterpret_cast<uint4*>(hb + (int64_t)ch * 2 * CHUNK + w * 16) =
+                        make_uint4(0, 0, 0, 0);
+                }
             }
         }
     }
@@ -314,7 +376,7 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
         dfree(tot, s);
         SP_TRY(dalloc((void**)&out->pairs, (size_t)(npairs > 0 ? npairs : 1) * PAIR_BYTES, s));
         if (npairs > 0) {
-            const int64_t want = (ne + 7) / 8;
+            const int64_t want = (ne + 255) / 256;
             const unsigned grid = (unsigned)(want < 8 * (int64_t)ctx->num_sms
                                                  ? want
                                                  : 8 * (int64_t)ctx->num_sms);
