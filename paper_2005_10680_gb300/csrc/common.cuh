@@ -118,13 +118,15 @@ int scan_i32_to_i64(spamm_ctx* ctx, const int32_t* d_in, int64_t* d_out, int64_t
                     unsigned long long* d_total);
 
 // Charge of the mixed-precision leaf products (see mixed.cu): per stored block,
-// slice norms sn[p] = ||X_p||_F and tail norms tn[p] >= ||X - sum_{q<=p} X_q||_F,
-// p = 1..S (S = MX_SLICES). A product formed from the level pairs p + q <= L,
-// 1 <= p, q <= S, leaves out
+// slice norms sn[p] >= ||X_p||_F and tail norms tn[p] >= ||X - sum_{q<=p} X_q||_F,
+// p = 1..S (S = MX_SLICES), stored as float32 rounded up. A product formed from the
+// level pairs p + q <= L, 1 <= p, q <= S, leaves out
 //   sum_{p=1}^{m} A_p (B - sum_{q <= min(L-p, S)} B_q) + (A - sum_{p<=m} A_p) B,
 // m = min(L - 1, S), so its error is at most
-//   sum_{p=1}^{m} snA[p] tnB[min(L-p, S)] + tnA[m] ||B_kj||_F.
-// lmax = 0 means "no charge" (float64 leaf products).
+//   sum_{p=1}^{m} snA[p] tnB[min(L-p, S)] + tnA[m] ||B_kj||_F,
+// evaluated in float32 with every rounding upward (all terms are non-negative, so
+// the result is at least the exact value; an underflow rounds up to the least
+// subnormal). lmax = 0 means "no charge" (float64 leaf products).
 constexpr int MX_SLICES = 9;      // digit slices per block in the mixed form
 constexpr int MIXED_LMAX = 11;    // highest level p + q the delta-searched mixed form forms
 
@@ -136,22 +138,23 @@ struct ChargeData {
     const int32_t* mapB = nullptr;
     const double* nA = nullptr;
     const double* nB = nullptr;
-    const double* snA = nullptr;
-    const double* tnA = nullptr;
-    const double* snB = nullptr;
-    const double* tnB = nullptr;
+    const float* snA = nullptr;
+    const float* tnA = nullptr;
+    const float* snB = nullptr;
+    const float* tnB = nullptr;
 };
 
 __device__ __forceinline__ double charge(const ChargeData& ch, int32_t sa, int32_t sb,
                                          double norm_b) {
     const int L = ch.lmax;
     const int m = L - 1 < MX_SLICES ? L - 1 : MX_SLICES;
-    const double* snA = ch.snA + (int64_t)sa * MX_SLICES;
-    const double* tnA = ch.tnA + (int64_t)sa * MX_SLICES;
-    const double* tnB = ch.tnB + (int64_t)sb * MX_SLICES;
-    double c = tnA[m - 1] * norm_b;
-    for (int p = 1; p <= m; ++p) c = fma(snA[p - 1], tnB[(L - p < MX_SLICES ? L - p : MX_SLICES) - 1], c);
-    return c;
+    const float* snA = ch.snA + (int64_t)sa * MX_SLICES;
+    const float* tnA = ch.tnA + (int64_t)sa * MX_SLICES;
+    const float* tnB = ch.tnB + (int64_t)sb * MX_SLICES;
+    float c = __fmul_ru(tnA[m - 1], __double2float_ru(norm_b));
+    for (int p = 1; p <= m; ++p)
+        c = __fmaf_ru(snA[p - 1], tnB[(L - p < MX_SLICES ? L - p : MX_SLICES) - 1], c);
+    return (double)c;
 }
 
 // slot of the B operand's slices for triple (i, k, j)

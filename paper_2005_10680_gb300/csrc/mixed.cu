@@ -52,52 +52,72 @@ constexpr int PAIR_BYTES = KCH * PAIR_CSTRIDE;   // 144 KB
 
 // rows (transpose = 0) or columns (transpose = 1) maxima of every stored block
 __global__ void k_block_rowmax(const double* __restrict__ tiles, const int32_t* __restrict__ coord,
-                               int transpose, float* __restrict__ out_unused,
-                               double* __restrict__ rmax) {
+                               int transpose, unsigned long long* __restrict__ rmax) {
+    // maxima of |x| as integers: for non-negative finite doubles the order of the bit
+    // patterns is the order of the values (integer pipe, not the slow float64 one)
     const int64_t s = blockIdx.x;
     const int t = threadIdx.x;   // 256
-    __shared__ double sh[4][64];
-    const double* T = tiles + s * MX_BS * MX_BS;
+    __shared__ unsigned long long sh[4][64];
+    const unsigned long long* T =
+        reinterpret_cast<const unsigned long long*>(tiles + s * MX_BS * MX_BS);
+    constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
     if (coord[s] < 0) {
-        if (t < 64) rmax[s * 64 + t] = 0.0;
+        if (t < 64) rmax[s * 64 + t] = 0ull;
         return;
     }
-    double m = 0.0;
     if (!transpose) {
         // warp w takes half rows w, w + 8, ...: 32 consecutive entries per load
         const int w = t >> 5, lane = t & 31;
-        double* hm = &sh[0][0];                  // [128] half-row maxima
+        unsigned long long* hm = &sh[0][0];      // [128] half-row maxima
         for (int hr = w; hr < 2 * MX_BS; hr += 8) {
-            double v = fabs(T[(hr >> 1) * MX_BS + (hr & 1) * 32 + lane]);
+            unsigned long long v = T[(hr >> 1) * MX_BS + (hr & 1) * 32 + lane] & ABS;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+                v = u > v ? u : v;
+            }
             if (lane == 0) hm[hr] = v;
         }
         __syncthreads();
-        if (t < 64) rmax[s * 64 + t] = fmax(hm[2 * t], hm[2 * t + 1]);
+        if (t < 64) {
+            const unsigned long long a = hm[2 * t], b = hm[2 * t + 1];
+            rmax[s * 64 + t] = a > b ? a : b;
+        }
     } else {
         const int col = t & 63, q = t >> 6;
-        for (int r = q * 16; r < q * 16 + 16; ++r) m = fmax(m, fabs(T[r * MX_BS + col]));
+        unsigned long long m = 0ull;
+        for (int r = q * 16; r < q * 16 + 16; ++r) {
+            const unsigned long long u = T[r * MX_BS + col] & ABS;
+            m = u > m ? u : m;
+        }
         sh[q][col] = m;
         __syncthreads();
-        if (t < 64) rmax[s * 64 + t] = fmax(fmax(sh[0][t], sh[1][t]), fmax(sh[2][t], sh[3][t]));
+        if (t < 64) {
+            unsigned long long v = sh[0][t];
+            for (int k = 1; k < 4; ++k) v = sh[k][t] > v ? sh[k][t] : v;
+            rmax[s * 64 + t] = v;
+        }
     }
 }
 
 // exponent of every row (columns when transpose): max |x| < 2^e, over the stored
 // blocks of the block row (block column) from its list
-__global__ void k_exponents(const double* __restrict__ rmax, const int32_t* __restrict__ map,
+__global__ void k_exponents(const unsigned long long* __restrict__ rmax, const int32_t* __restrict__ map,
                             int nb, int transpose, const int64_t* __restrict__ lptr,
                             const int32_t* __restrict__ lidx, int32_t* __restrict__ expo) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= (int64_t)nb * MX_BS) return;
     const int rb = (int)(r / MX_BS), rr = (int)(r % MX_BS);
-    double m = 0.0;
+    unsigned long long mb = 0ull;
     for (int64_t q = lptr[rb]; q < lptr[rb + 1]; ++q) {
         const int o = lidx[q];
         const int32_t s = transpose ? map[(int64_t)o * nb + rb] : map[(int64_t)rb * nb + o];
-        if (s >= 0) m = fmax(m, rmax[(int64_t)s * 64 + rr]);
+        if (s >= 0) {
+            const unsigned long long u = rmax[(int64_t)s * 64 + rr];
+            mb = u > mb ? u : mb;
+        }
     }
+    const double m = __longlong_as_double((long long)mb);
     int e = 0;
     if (m > 0.0) frexp(m, &e);   // m = f 2^e, f in [0.5, 1): m < 2^e
     expo[r] = e;
@@ -134,8 +154,8 @@ __device__ __forceinline__ double pow2_exact(int e) {
 __global__ void __launch_bounds__(256, 3)
 k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
         const int32_t* __restrict__ expo, uint8_t* __restrict__ pairs,
-        const int64_t* __restrict__ pair_idx, int8_t* __restrict__ p0, double* __restrict__ sn,
-        double* __restrict__ tn) {
+        const int64_t* __restrict__ pair_idx, int8_t* __restrict__ p0, float* __restrict__ sn,
+        float* __restrict__ tn) {
     const int64_t s = blockIdx.x;
     const int t = threadIdx.x;
     __shared__ double T[MX_BS][MX_BS + 1];
@@ -261,9 +281,11 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                     (double)row_r[lane + 32][p] * pow2_exact(2 * (e1 - MX_W * MX_S));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            // float32 rounded up, after a 2^-40 margin for the float64 sums and root
             if (lane == 0) {
-                if (warp == 0) sn[s * MX_S + p] = sqrt(v);
-                else tn[s * MX_S + p] = sqrt(v * (1.0 + 0x1p-12)) * (1.0 + 0x1p-40);
+                if (warp == 0) sn[s * MX_S + p] = __double2float_ru(sqrt(v) * (1.0 + 0x1p-40));
+                else tn[s * MX_S + p] =
+                    __double2float_ru(sqrt(v * (1.0 + 0x1p-12)) * (1.0 + 0x1p-40));
             }
         }
     }
@@ -274,8 +296,8 @@ struct SliceSet {
     uint8_t* pairs = nullptr;       // pair tiles (A operand)
     int64_t* pair_idx = nullptr;    // [(nb + 1) / 2 * nb]: pair tile of (I, k), or -1
     int8_t* p0 = nullptr;
-    double* sn = nullptr;
-    double* tn = nullptr;
+    float* sn = nullptr;         // slice norms, float32 rounded up
+    float* tn = nullptr;         // tail norms, float32 rounded up
     int32_t* expo = nullptr;
     void free(cudaStream_t s) {
         dfree(pairs, s);
@@ -386,15 +408,15 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
         }
     }
     SP_TRY(dalloc((void**)&out->p0, (size_t)ns, s));
-    SP_TRY(dalloc((void**)&out->sn, sizeof(double) * ns * MX_S, s));
-    SP_TRY(dalloc((void**)&out->tn, sizeof(double) * ns * MX_S, s));
+    SP_TRY(dalloc((void**)&out->sn, sizeof(float) * ns * MX_S, s));
+    SP_TRY(dalloc((void**)&out->tn, sizeof(float) * ns * MX_S, s));
     SP_TRY(dalloc((void**)&out->expo, sizeof(int32_t) * (size_t)X->nb * MX_BS, s));
-    double* rmax = nullptr;
-    SP_TRY(dalloc((void**)&rmax, sizeof(double) * ns * 64, s));
+    unsigned long long* rmax = nullptr;   // bit patterns of the row maxima of |x|
+    SP_TRY(dalloc((void**)&rmax, sizeof(unsigned long long) * ns * 64, s));
     if (X->nslots > 0) {
         ++ctx->launches;
         k_block_rowmax<<<(unsigned)X->nslots, 256, 0, s>>>(X->d_tiles, X->d_coord, transpose,
-                                                           nullptr, rmax);
+                                                           rmax);
     }
     const int64_t rows = (int64_t)X->nb * MX_BS;
     BlockLists lists;   // the stored blocks of every block row (block column)
