@@ -133,9 +133,9 @@ __global__ void k_exponents(const unsigned long long* __restrict__ rmax, const i
 // digits d_p + 64 (p >= 2) in plain base 128, so every digit (and every tail
 // R_p = sum_{q>p} d_q 2^(7 (9 - q)) = (low 7 (9 - p) bits) - C_p) is computed
 // independently of the others. Slice norms are exact (digit squares summed exactly
-// per row in f32); tail norms are upper bounds: |R_p| per entry, plus 1/2 where the
-// rounding of V was inexact, summed in f32 and inflated by 2^-12 to cover the f32
-// rounding. transpose: slice the transposed block with column exponents. The digits
+// per row in f32); tail norms are upper bounds: |R_p| per entry (converted to f32
+// rounded up), plus 1/2 where the rounding of V was inexact, summed in f32 and
+// inflated by 2^-12 to cover the f32 rounding. transpose: slice the transposed block with column exponents. The digits
 // go to the block's half of its pair tile.
 constexpr unsigned long long M56 = (1ull << 56) - 1;
 
@@ -143,6 +143,60 @@ __host__ __device__ constexpr unsigned long long digit_offset(int low_digits) {
     // 64 * (128^low_digits - 1) / 127: the offset that makes low_digits balanced
     // base-128 digits non-negative
     return 64ull * (((1ull << (7 * low_digits)) - 1ull) / 127ull);
+}
+
+// v 2^ex rounded to the nearest double (ties to even), from the integer's bits: the
+// int64 -> double conversion and the scaling multiply would both run on the slow
+// float64 pipe. Results that are not normal doubles take the arithmetic path.
+__device__ __forceinline__ double i64_scaled_to_double(long long v, int ex) {
+    if (v == 0) return 0.0;
+    const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
+    const int msb = 63 - __clzll((long long)a);
+    int e = msb + ex;                             // exponent of the leading bit
+    if (e < -1022 || e > 1022) return ldexp((double)v, ex);
+    unsigned long long m;
+    if (msb <= 52) {
+        m = a << (52 - msb);                      // exact
+    } else {
+        const int sh = msb - 52;
+        m = a >> sh;
+        const unsigned long long rem = a & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) {
+            m += 1ull;
+            if (m == (1ull << 53)) {              // rounded up to the next power of two
+                m >>= 1;
+                e += 1;
+            }
+        }
+    }
+    const unsigned long long bits = (v < 0 ? 0x8000000000000000ull : 0ull) |
+                                    ((unsigned long long)(e + 1023) << 52) |
+                                    (m & ((1ull << 52) - 1ull));
+    return __longlong_as_double((long long)bits);
+}
+
+// float32 of a non-negative integer below 2^64, rounded up, from its bits alone (the
+// integer pipe: an int64 -> float conversion runs on the slow float64 unit)
+__device__ __forceinline__ float u64_to_float_ru(unsigned long long a) {
+    if (a == 0ull) return 0.f;
+    const int msb = 63 - __clzll((long long)a);
+    unsigned long long mant;
+    bool rest = false;
+    if (msb <= 23) {
+        mant = a << (23 - msb);
+    } else {
+        const int sh = msb - 23;
+        mant = a >> sh;
+        rest = (a & ((1ull << sh) - 1ull)) != 0ull;
+    }
+    unsigned int bits = ((unsigned int)(msb + 127) << 23) | ((unsigned int)mant & 0x7FFFFFu);
+    if (rest) bits += 1u;                         // round up (a carry moves into the exponent)
+    return __uint_as_float(bits);
+}
+
+// float32 of a small integer |d| < 2^22, exactly, by the 1.5 * 2^23 offset
+__device__ __forceinline__ float small_int_to_float(int d) {
+    return __int_as_float(0x4B400000 + d) - 12582912.0f;
 }
 
 __device__ __forceinline__ double pow2_exact(int e) {
@@ -229,13 +283,16 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                     const int low = MX_S - 1 - p;
                     const long long Rp =
                         (long long)(L & ((1ull << (MX_W * low)) - 1ull)) - (long long)digit_offset(low);
-                    const float rf = fabsf((float)Rp) + half;
+                    const float rf =
+                        u64_to_float_ru((unsigned long long)(Rp < 0 ? -Rp : Rp)) + half;
                     sr[p] = fmaf(rf, rf, sr[p]);
                 }
-                sa[p] = fmaf((float)d, (float)d, sa[p]);
+                const float fd = small_int_to_float(d);   // exact: |d| <= 128
+                sa[p] = fmaf(fd, fd, sa[p]);
                 if (d != 0 && p + 1 < firstp) firstp = p + 1;
-                pk[p][e >> 1] |= (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)d))
-                                 << (16 * (e & 1));
+                // bf16 of an integer of at most 8 significant bits: the top half of its
+                // float32 bits, exactly
+                pk[p][e >> 1] |= (__float_as_uint(fd) >> 16) << (16 * (e & 1));
             }
             sr[MX_S - 1] += half * half;           // tail after all digits: |T_S| <= 1/2 unit
         }
@@ -721,7 +778,7 @@ struct TileArgs {
 // 128 x 128 in TMEM, folded every `window` leaf products into one int64 per entry,
 // V = sum_lv g_lv 2^(7 (HI - lv)), |g_lv| < 2^24 per window.
 template <int LO, int HI>
-__global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
+__global__ void __maxnreg__(112) k_gemm_tile(TileArgs a) {
     using PS = PassShape<LO, HI>;
     static_assert(HI - LO < MAX_LEVELS && LO >= 2 && HI <= 2 * MX_S, "levels must fit in TMEM");
     constexpr int SMAX = PS::SMAX, HALF = PS::HALF, STAGE = PS::STAGE, NST = PS::NST;
@@ -962,12 +1019,9 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
             for (int j = 0; j < 32; ++j) {
                 const int sc = sc0 + j;
                 const int fs = a.expB[bj * MX_BS + sc];
-                // V 2^e: a multiply by the power of two when 2^e is a normal double
+                // V 2^e, correctly rounded, built from the integer's bits
                 const int ex = er + fs - MX_W * HI;
-                const double vf = (double)acc[j];
-                double cv = (ex >= -1022 && ex <= 1023)
-                                ? vf * __longlong_as_double((long long)(ex + 1023) << 52)
-                                : ldexp(vf, ex);
+                double cv = i64_scaled_to_double(acc[j], ex);
                 if (a.add_prev && Co) cv += Co[rr * MX_BS + sc];
                 if (a.raw_out) {
                     if (Co) Co[rr * MX_BS + sc] = cv;
