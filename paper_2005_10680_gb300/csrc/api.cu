@@ -107,7 +107,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         cudaEventRecord(ctx->ev[EV_CSE0], s);
         // fewest levels whose certified charge (everything formed, tau = 0) stays
         // within half of delta: the charge shrinks as levels are added, so bisect over
-        // L in [4, 11]; with a given tau every level up to 10 is formed. At L = 11 the
+        // L in [4, 13]; with a given tau every level up to 10 is formed. At L = 13 the
         // charge may take up to 0.9 delta (the tau search still certifies the sum of
         // charges and skipped products below delta).
         lmax_used = 0;

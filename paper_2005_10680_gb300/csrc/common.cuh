@@ -128,7 +128,7 @@ int scan_i32_to_i64(spamm_ctx* ctx, const int32_t* d_in, int64_t* d_out, int64_t
 // the result is at least the exact value; an underflow rounds up to the least
 // subnormal). lmax = 0 means "no charge" (float64 leaf products).
 constexpr int MX_SLICES = 9;      // digit slices per block in the mixed form
-constexpr int MIXED_LMAX = 11;    // highest level p + q the delta-searched mixed form forms
+constexpr int MIXED_LMAX = 13;    // highest level p + q the delta-searched mixed form forms
 
 struct ChargeData {
     int nb = 0;

@@ -148,12 +148,14 @@ __host__ __device__ constexpr unsigned long long digit_offset(int low_digits) {
 // v 2^ex rounded to the nearest double (ties to even), from the integer's bits: the
 // int64 -> double conversion and the scaling multiply would both run on the slow
 // float64 pipe. Results that are not normal doubles take the arithmetic path.
+__device__ __noinline__ double i64_scaled_slow(long long v, int ex) { return ldexp((double)v, ex); }
+
 __device__ __forceinline__ double i64_scaled_to_double(long long v, int ex) {
     if (v == 0) return 0.0;
     const unsigned long long a = v < 0 ? 0ull - (unsigned long long)v : (unsigned long long)v;
     const int msb = 63 - __clzll((long long)a);
     int e = msb + ex;                             // exponent of the leading bit
-    if (e < -1022 || e > 1022) return ldexp((double)v, ex);
+    if (e < -1022 || e > 1022) return i64_scaled_slow(v, ex);
     unsigned long long m;
     if (msb <= 52) {
         m = a << (52 - msb);                      // exact
@@ -778,7 +780,7 @@ struct TileArgs {
 // 128 x 128 in TMEM, folded every `window` leaf products into one int64 per entry,
 // V = sum_lv g_lv 2^(7 (HI - lv)), |g_lv| < 2^24 per window.
 template <int LO, int HI>
-__global__ void __maxnreg__(112) k_gemm_tile(TileArgs a) {
+__global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
     using PS = PassShape<LO, HI>;
     static_assert(HI - LO < MAX_LEVELS && LO >= 2 && HI <= 2 * MX_S, "levels must fit in TMEM");
     constexpr int SMAX = PS::SMAX, HALF = PS::HALF, STAGE = PS::STAGE, NST = PS::NST;
@@ -1088,7 +1090,7 @@ struct PassKernel {
 };
 
 // the instance for levels lo..hi: lo = 2 (hi = 4, 5), lo = 6 (hi = 6..9), lo = 10
-// (hi = 10, 11)
+// (hi = 10..13)
 static PassKernel pass_kernel(int lo, int hi) {
 #define SPAMM_PASS(L, H) PassKernel{k_gemm_tile<L, H>, PassShape<L, H>::SMEM}
     if (lo == 2) return hi <= 4 ? SPAMM_PASS(2, 4) : SPAMM_PASS(2, 5);
@@ -1100,10 +1102,15 @@ static PassKernel pass_kernel(int lo, int hi) {
             default: return SPAMM_PASS(6, 9);
         }
     }
-    return hi <= 10 ? SPAMM_PASS(10, 10) : SPAMM_PASS(10, 11);
+    switch (hi) {
+        case 10: return SPAMM_PASS(10, 10);
+        case 11: return SPAMM_PASS(10, 11);
+        case 12: return SPAMM_PASS(10, 12);
+        default: return SPAMM_PASS(10, 13);
+    }
 #undef SPAMM_PASS
 }
-static_assert(MIXED_LMAX == 11, "the pass instances cover levels 2..11");
+static_assert(MIXED_LMAX == 13, "the pass instances cover levels 2..13");
 
 static bool g_attr_set[64] = {false};
 static std::mutex g_mixed_init;   // one-time per-device set-up, shared by host threads
@@ -1112,7 +1119,8 @@ static int set_pass_attributes(spamm_ctx* ctx) {
     std::lock_guard<std::mutex> lock(g_mixed_init);
     if (ctx->device < 0 || ctx->device >= 64) return SPAMM_EINVAL;
     if (g_attr_set[ctx->device]) return SPAMM_OK;
-    const int ranges[8][2] = {{2, 4}, {2, 5}, {6, 6}, {6, 7}, {6, 8}, {6, 9}, {10, 10}, {10, 11}};
+    const int ranges[10][2] = {{2, 4},  {2, 5},   {6, 6},   {6, 7},   {6, 8},
+                               {6, 9},  {10, 10}, {10, 11}, {10, 12}, {10, 13}};
     for (const auto& r : ranges) {
         const PassKernel k = pass_kernel(r[0], r[1]);
         SP_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, k.smem));
