@@ -235,12 +235,12 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
     float sa[MX_S], sr[MX_S];                     // per-thread sums of d_p^2 and (|R_p| + 1/2)^2
 #pragma unroll
     for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.f;
-    int firstp = MX_S + 1;
     // pairing along block rows (transpose = 0) or block columns (transpose = 1)
     const int pr = transpose ? bj : bi, pk = transpose ? bi : bj;
     uint8_t* pout =
         pairs + pair_idx[(int64_t)(pr >> 1) * nb + pk] * (int64_t)PAIR_BYTES + (pr & 1) * CHUNK;
-#pragma unroll
+    unsigned nz = 0u;                             // bit p: some entry has a nonzero digit p + 1
+#pragma unroll 1
     for (int g2 = 0; g2 < 2; ++g2) {
         const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
         uint32_t pk[MX_S][4];                      // bf16 pairs of the 8 values, per slice
@@ -275,26 +275,38 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             const float half = inexact ? 0.5f : 0.f;
             // V = hi 2^56 + lo, lo in [0, 2^56); lo + C = carry 2^56 + L with L the digits + 64
             const unsigned long long tt = ((unsigned long long)V & M56) + digit_offset(8);
-            const unsigned long long L = tt & M56;
+            const unsigned int Llo = (unsigned int)tt, Lhi = (unsigned int)(tt >> 32) & 0xFFFFFFu;
             const int d1 = (int)(V >> 56) + (int)(tt >> 56);
+            int d[MX_S];
+            d[0] = d1;
 #pragma unroll
-            for (int p = 0; p < MX_S; ++p) {       // slice p + 1
-                const int d = p == 0 ? d1 : (int)((L >> (MX_W * (MX_S - 1 - p))) & 127ull) - 64;
-                if (p < MX_S - 1) {
-                    // tail after digit p + 1 (in units of 2^(e_r - 63)): the digits below it
-                    const int low = MX_S - 1 - p;
-                    const long long Rp =
-                        (long long)(L & ((1ull << (MX_W * low)) - 1ull)) - (long long)digit_offset(low);
-                    const float rf =
-                        u64_to_float_ru((unsigned long long)(Rp < 0 ? -Rp : Rp)) + half;
-                    sr[p] = fmaf(rf, rf, sr[p]);
-                }
-                const float fd = small_int_to_float(d);   // exact: |d| <= 128
+            for (int p = 1; p < MX_S; ++p) {       // digit p + 1 sits at bits 7 (8 - p)
+                const int at = MX_W * (MX_S - 1 - p);
+                unsigned int f;
+                if (at + 7 <= 32) f = (Llo >> at) & 127u;
+                else if (at >= 32) f = (Lhi >> (at - 32)) & 127u;
+                else f = __funnelshift_r(Llo, Lhi, at) & 127u;
+                d[p] = (int)f - 64;
+            }
+            // tails from the bottom: R_8 = d_9, R_p = d_(p+1) 128^(8 - p) + R_(p+1). Each
+            // step is one rounding of a sum whose magnitude is at least half of its
+            // larger term (balanced digits), so the relative error of |R_p| stays below
+            // 2^-21, inside the 2^-12 inflation of the tail norms
+            float r = 0.f;
+#pragma unroll
+            for (int p = MX_S - 1; p >= 0; --p) {  // slice p + 1
+                const float fd = small_int_to_float(d[p]);   // exact: |d| <= 128
                 sa[p] = fmaf(fd, fd, sa[p]);
-                if (d != 0 && p + 1 < firstp) firstp = p + 1;
+                nz |= (d[p] != 0 ? 1u : 0u) << p;
                 // bf16 of an integer of at most 8 significant bits: the top half of its
                 // float32 bits, exactly
                 pk[p][e >> 1] |= (__float_as_uint(fd) >> 16) << (16 * (e & 1));
+                if (p < MX_S - 1) {
+                    // tail after digit p + 1 (units of 2^(e_r - 63)): r holds R_(p+1)
+                    const float rf = fabsf(r) + half;
+                    sr[p] = fmaf(rf, rf, sr[p]);
+                }
+                if (p > 0) r = fmaf(fd, (float)(1u << (MX_W * (MX_S - 1 - p))), r);
             }
             sr[MX_S - 1] += half * half;           // tail after all digits: |T_S| <= 1/2 unit
         }
@@ -305,6 +317,7 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
         }
     }
+    const int firstp = nz ? __ffs((int)nz) : MX_S + 1;
     // per-row sums over the row's 4 lanes, in f32: exact for the digit squares (integers
     // below 2^24), covered by the 2^-12 inflation for the tails
 #pragma unroll
@@ -508,26 +521,21 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
 // Task: (pair tile of A at (I, k), pair tile of the B operand at (J, k), pa | qb << 8)
 // with pa, qb the first nonzero slices over the tile's stored blocks.
 
-// Tiles are enumerated in L2-friendly order: supertiles of IT x JT tiles (about one
-// wave of CTAs), the column index fastest inside a supertile, so that the CTAs of a
-// wave share IT pair tiles of A and JT of B while they all walk k upwards.
+// Tiles are enumerated in L2-friendly order (Raster): the CTAs of a wave share the
+// pair tiles of A and B of a compact group of tiles while they all walk k upwards.
 struct Raster {
-    int np, it, jt, nsj;
-    __host__ __device__ int64_t size() const {
-        return (int64_t)((np + it - 1) / it) * it * (int64_t)nsj * jt;
-    }
+    // Z order (Morton) of the tile grid: the work items are numbered in the order of
+    // their interleaved (I, J) bits, so the CTAs that run together cover a compact
+    // square of tiles at every scale, dense or sparse, and share the pair tiles of
+    // their few pair rows and pair columns through L2
+    int np;          // pair rows (= pair columns)
+    int bits;        // 2^bits >= np
+    __host__ __device__ int64_t size() const { return (int64_t)1 << (2 * bits); }
     __device__ int64_t index(int I, int J) const {
-        const int64_t st = (int64_t)(I / it) * nsj + J / jt;
-        return st * ((int64_t)it * jt) + (int64_t)(I % it) * jt + J % jt;
-    }
-    __device__ bool unswizzle(int64_t b, int* I, int* J) const {
-        const int64_t per = (int64_t)it * jt;
-        const int64_t st = b / per;
-        const int r = (int)(b % per);
-        const int sI = (int)(st / nsj), sJ = (int)(st % nsj);
-        *I = sI * it + r / jt;
-        *J = sJ * jt + r % jt;
-        return *I < np && *J < np;
+        int64_t z = 0;
+        for (int b = 0; b < bits; ++b)
+            z |= ((int64_t)((J >> b) & 1) << (2 * b)) | ((int64_t)((I >> b) & 1) << (2 * b + 1));
+        return z;
     }
 };
 
@@ -1225,9 +1233,8 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
     tp.lmax = lmax;
     Raster rs;
     rs.np = np;
-    rs.it = 8;
-    rs.jt = (ctx->num_sms + 7) / 8;
-    rs.nsj = (np + rs.jt - 1) / rs.jt;
+    rs.bits = 0;
+    while ((1 << rs.bits) < np) ++rs.bits;
     const int64_t ntile = rs.size();
     int32_t *cnt = nullptr, *wf = nullptr, *of = nullptr;
     int64_t *toff = nullptr, *widx = nullptr, *oidx = nullptr;
