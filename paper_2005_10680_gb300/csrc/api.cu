@@ -312,26 +312,31 @@ __global__ void k_x0_flags(const int32_t* __restrict__ mapF, int nb, int32_t* fl
     flag[b] = (mapF[b] >= 0 || (b / nb) == (b % nb)) ? 1 : 0;
 }
 
-__global__ void k_x0_fill(const double* __restrict__ tilesF, const int32_t* __restrict__ mapF,
-                          const int32_t* __restrict__ flag, const int64_t* __restrict__ slot,
-                          int nb, int bs, int64_t n, double lmax, double width,
-                          int32_t* __restrict__ map, int32_t* __restrict__ coord,
-                          double* __restrict__ tiles) {
-    const int64_t b = blockIdx.x;
-    if (!flag[b]) return;
-    const int bi = (int)(b / nb), bj = (int)(b % nb);
+// slot and coordinates of every block of X_0's pattern (from the scan of the flags)
+__global__ void k_x0_index(const int32_t* __restrict__ flag, const int64_t* __restrict__ slot,
+                           int64_t nb2, int32_t* __restrict__ map, int32_t* __restrict__ coord) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb2 || !flag[b]) return;
     const int64_t s = slot[b];
+    map[b] = (int32_t)s;
+    coord[s] = (int32_t)b;
+}
+
+// one CTA per block of X_0: X_0 = lmax / width I - F / width (a multiply by the
+// reciprocal of the width)
+__global__ void k_x0_fill(const double* __restrict__ tilesF, const int32_t* __restrict__ mapF,
+                          const int32_t* __restrict__ coord, int nb, int bs, int64_t n,
+                          double diag, double inv_width, double* __restrict__ tiles) {
+    const int64_t s = blockIdx.x;
+    const int32_t b = coord[s];
+    const int bi = b / nb, bj = b % nb;
     const int32_t sf = mapF[b];
     double* t = tiles + s * (int64_t)bs * bs;
     for (int e = threadIdx.x; e < bs * bs; e += blockDim.x) {
         const int r = e / bs, c = e % bs;
-        double x = sf >= 0 ? -tilesF[(int64_t)sf * bs * bs + e] / width : 0.0;
-        if (bi == bj && r == c && (int64_t)bi * bs + r < n) x += lmax / width;
+        double x = sf >= 0 ? -tilesF[(int64_t)sf * bs * bs + e] * inv_width : 0.0;
+        if (bi == bj && r == c && (int64_t)bi * bs + r < n) x += diag;
         t[e] = x;
-    }
-    if (threadIdx.x == 0) {
-        map[b] = (int32_t)s;
-        coord[s] = (int32_t)b;
     }
 }
 
@@ -354,9 +359,12 @@ int make_x0(spamm_ctx* ctx, const spamm_mat* F, double lmin, double lmax, spamm_
     spamm_mat* X = nullptr;
     SP_TRY(mat_alloc(ctx, F->n, F->bs, (int64_t)cnt, &X));
     X->nslots = X->nnzb = (int64_t)cnt;
-    ++ctx->launches;
-    k_x0_fill<<<(unsigned)nb2, 256, 0, s>>>(F->d_tiles, F->d_map, flag, slot, nb, F->bs, F->n,
-                                            lmax, lmax - lmin, X->d_map, X->d_coord, X->d_tiles);
+    ctx->launches += 2;
+    k_x0_index<<<(unsigned)((nb2 + 255) / 256), 256, 0, s>>>(flag, slot, nb2, X->d_map, X->d_coord);
+    if (cnt > 0)
+        k_x0_fill<<<(unsigned)cnt, 256, 0, s>>>(F->d_tiles, F->d_map, X->d_coord, nb, F->bs, F->n,
+                                                lmax / (lmax - lmin), 1.0 / (lmax - lmin),
+                                                X->d_tiles);
     SP_CHECK_LAUNCH();
     SP_TRY(mat_compute_norms(ctx, X));
     dfree(flag, s);

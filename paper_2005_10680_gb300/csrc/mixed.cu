@@ -177,25 +177,6 @@ __device__ __forceinline__ double i64_scaled_to_double(long long v, int ex) {
     return __longlong_as_double((long long)bits);
 }
 
-// float32 of a non-negative integer below 2^64, rounded up, from its bits alone (the
-// integer pipe: an int64 -> float conversion runs on the slow float64 unit)
-__device__ __forceinline__ float u64_to_float_ru(unsigned long long a) {
-    if (a == 0ull) return 0.f;
-    const int msb = 63 - __clzll((long long)a);
-    unsigned long long mant;
-    bool rest = false;
-    if (msb <= 23) {
-        mant = a << (23 - msb);
-    } else {
-        const int sh = msb - 23;
-        mant = a >> sh;
-        rest = (a & ((1ull << sh) - 1ull)) != 0ull;
-    }
-    unsigned int bits = ((unsigned int)(msb + 127) << 23) | ((unsigned int)mant & 0x7FFFFFu);
-    if (rest) bits += 1u;                         // round up (a carry moves into the exponent)
-    return __uint_as_float(bits);
-}
-
 // float32 of a small integer |d| < 2^22, exactly, by the 1.5 * 2^23 offset
 __device__ __forceinline__ float small_int_to_float(int d) {
     return __int_as_float(0x4B400000 + d) - 12582912.0f;
@@ -306,7 +287,8 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                     const float rf = fabsf(r) + half;
                     sr[p] = fmaf(rf, rf, sr[p]);
                 }
-                if (p > 0) r = fmaf(fd, (float)(1u << (MX_W * (MX_S - 1 - p))), r);
+                // weight of digit p + 1: 128^(8 - p) = 2^(7 (8 - p)), an exact float32
+                if (p > 0) r = fmaf(fd, __int_as_float((127 + MX_W * (MX_S - 1 - p)) << 23), r);
             }
             sr[MX_S - 1] += half * half;           // tail after all digits: |T_S| <= 1/2 unit
         }
