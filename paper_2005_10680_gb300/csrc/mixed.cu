@@ -177,6 +177,55 @@ __device__ __forceinline__ double i64_scaled_to_double(long long v, int ex) {
     return __longlong_as_double((long long)bits);
 }
 
+// v 2^ex rounded to the nearest double (ties to even) for a 128-bit integer, from its
+// bits (the exact sum of two passes' int64 sums, one of them shifted by 7 levels each)
+__device__ __noinline__ double i128_scaled_slow(long long hi, unsigned long long lo, int ex) {
+    return ldexp((double)hi * 18446744073709551616.0 + (double)lo, ex);
+}
+
+__device__ __forceinline__ double i128_scaled_to_double(__int128 v, int ex) {
+    const bool neg = v < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    if (hi == 0ull && lo < (1ull << 62))
+        return i64_scaled_to_double(neg ? -(long long)lo : (long long)lo, ex);
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    int e = msb + ex;
+    if (e < -1022 || e > 1022) return i128_scaled_slow((long long)(v >> 64), (unsigned long long)v, ex);
+    const int sh = msb - 52;                      // >= 10
+    unsigned long long m = (unsigned long long)(a >> sh);
+    const unsigned __int128 rem = a & (((unsigned __int128)1 << sh) - 1u);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+        m += 1ull;
+        if (m == (1ull << 53)) {
+            m >>= 1;
+            e += 1;
+        }
+    }
+    const unsigned long long bits = (neg ? 0x8000000000000000ull : 0ull) |
+                                    ((unsigned long long)(e + 1023) << 52) |
+                                    (m & ((1ull << 52) - 1ull));
+    return __longlong_as_double((long long)bits);
+}
+
+// |x| as float32 rounded up, from its bits; only for |x| < 2^56 (the caller checks),
+// below 2^-126 it returns 2^-126 (or 0 for 0)
+__device__ __forceinline__ float abs_f64_to_f32_ru(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    const int ef = (int)(b >> 52) - 1023 + 127;
+    if (ef <= 0) return b == 0ull ? 0.f : 1.17549435e-38f;
+    unsigned int fb = ((unsigned int)ef << 23) | ((unsigned int)(b >> 29) & 0x7FFFFFu);
+    if (b & ((1ull << 29) - 1ull)) fb += 1u;      // round up
+    return __uint_as_float(fb);
+}
+
+// |x| < 2^56: its square, and a sum of 4096 such squares, stay inside float32
+__device__ __forceinline__ bool f32_square_safe(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) <
+           0x4370000000000000ull;   // 2^56
+}
+
 // float32 of a small integer |d| < 2^22, exactly, by the 1.5 * 2^23 offset
 __device__ __forceinline__ float small_int_to_float(int d) {
     return __int_as_float(0x4B400000 + d) - 12582912.0f;
@@ -754,8 +803,13 @@ struct TileArgs {
     int nb, np;
     int window;                  // leaf products per exact-accumulation window
     int mode;                    // 0: C; 1: Xn = C; 2: Xn = 2X - C
-    int raw_out;                 // 1: write this pass's raw product (plus add_prev) and stop
-    int add_prev;                // 1: add the raw product already in the output slots
+    int raw_out;                 // 1: write this pass's product as float64 (plus what the
+                                 //    output slots hold) and stop
+    int add_prev;                // 1: add the float64 partial already in the output slots
+    int out_int;                 // 1: write this pass's raw int64 sums and stop
+    int prev_int;                // 1: the output slots hold the raw int64 sums of the pass
+                                 //    with top level prev_hi: combine them exactly
+    int prev_hi;
     const int32_t* mapX;
     const double* tilesX;
     double* tilesC;
@@ -773,6 +827,7 @@ template <int LO, int HI>
 __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
     using PS = PassShape<LO, HI>;
     static_assert(HI - LO < MAX_LEVELS && LO >= 2 && HI <= 2 * MX_S, "levels must fit in TMEM");
+    static_assert(PS::NST * PS::STAGE >= 512 * 32 * 8, "the epilogue stages its sums in the ring");
     constexpr int SMAX = PS::SMAX, HALF = PS::HALF, STAGE = PS::STAGE, NST = PS::NST;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* stages = smem;
@@ -988,6 +1043,13 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
             if (lane == 0) tc::mbar_arrive(b_acce);
         }
         // ---- values, SP2 combination, writes, partial sums
+        // Every MMA and bulk copy of this tile has completed (the last window was
+        // waited for), so the stage ring is free: the sums move there, one slot per
+        // column and thread (conflict-free), and the loop below keeps few registers.
+        long long* accs = reinterpret_cast<long long*>(stages);
+        const int et = tid - 64;                  // 0..511
+#pragma unroll
+        for (int j = 0; j < 32; ++j) accs[j * 512 + et] = acc[j];
         const int nb = a.nb;
         const int32_t ij = a.work_ij[w];
         const int I = ij / a.np, J = ij % a.np;
@@ -995,6 +1057,9 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
         const int h = rl >> 6, rr = rl & 63;
         const int cc = cb >> 1, sc0 = (cb & 1) * 32;
         const int bi = 2 * I + h, bj = 2 * J + cc;
+        // squared norms: float32 rounded up (upper bounds) for entries below 2^56, a
+        // float64 sum for larger ones
+        float fro2f = 0.f, idem2f = 0.f;
         double fro2 = 0.0, tr = 0.0, idem2 = 0.0;
         if (bi < nb && bj < nb) {
             const int32_t os = a.work_out[8 * w + 2 * h + cc];
@@ -1007,13 +1072,30 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
             }
             double* Co = os >= 0 ? a.tilesC + (int64_t)os * MX_BS * MX_BS : nullptr;
             double* Ct = ost >= 0 ? a.tilesC + (int64_t)ost * MX_BS * MX_BS : nullptr;
-#pragma unroll
+#pragma unroll 2
             for (int j = 0; j < 32; ++j) {
                 const int sc = sc0 + j;
                 const int fs = a.expB[bj * MX_BS + sc];
-                // V 2^e, correctly rounded, built from the integer's bits
-                const int ex = er + fs - MX_W * HI;
-                double cv = i64_scaled_to_double(acc[j], ex);
+                const long long aj = accs[j * 512 + et];
+                if (a.out_int) {
+                    // raw int64 sums, for the last pass to combine exactly
+                    if (Co) reinterpret_cast<long long*>(Co)[rr * MX_BS + sc] = aj;
+                    continue;
+                }
+                // V 2^e, correctly rounded, built from the integer's bits; with the raw
+                // sums of an earlier pass the two are first added exactly in 128 bits
+                double cv;
+                if (a.prev_int && Co) {
+                    const long long vp = reinterpret_cast<const long long*>(Co)[rr * MX_BS + sc];
+                    const int hmax = HI > a.prev_hi ? HI : a.prev_hi;
+                    const __int128 t =
+                        HI > a.prev_hi
+                            ? (__int128)aj + ((__int128)vp << (MX_W * (HI - a.prev_hi)))
+                            : (__int128)vp + ((__int128)aj << (MX_W * (a.prev_hi - HI)));
+                    cv = i128_scaled_to_double(t, er + fs - MX_W * hmax);
+                } else {
+                    cv = i64_scaled_to_double(aj, er + fs - MX_W * HI);
+                }
                 if (a.add_prev && Co) cv += Co[rr * MX_BS + sc];
                 if (a.raw_out) {
                     if (Co) Co[rr * MX_BS + sc] = cv;
@@ -1021,18 +1103,40 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
                 }
                 const double x = X ? X[rr * MX_BS + sc] : 0.0;
                 const double out = a.mode == 2 ? 2.0 * x - cv : cv;
-                if (a.mode != 0) idem2 = fma(cv - x, cv - x, idem2);
-                fro2 = fma(out, out, fro2);
+                if (a.mode != 0) {
+                    const double dcx = cv - x;
+                    if (f32_square_safe(dcx)) {
+                        const float f = abs_f64_to_f32_ru(dcx);
+                        idem2f = __fmaf_ru(f, f, idem2f);
+                    } else {
+                        idem2 = fma(dcx, dcx, idem2);
+                    }
+                }
+                if (f32_square_safe(out)) {
+                    const float f = abs_f64_to_f32_ru(out);
+                    fro2f = __fmaf_ru(f, f, fro2f);
+                } else {
+                    fro2 = fma(out, out, fro2);
+                }
                 if (bi == bj && rr == sc) tr += out;
                 if (Co) Co[rr * MX_BS + sc] = out;
                 if (Ct) Ct[sc * MX_BS + rr] = out;
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            fro2 += __shfl_xor_sync(0xffffffffu, fro2, o);
-            tr += __shfl_xor_sync(0xffffffffu, tr, o);
-            idem2 += __shfl_xor_sync(0xffffffffu, idem2, o);
+            fro2f = __fadd_ru(fro2f, __shfl_xor_sync(0xffffffffu, fro2f, o));
+            idem2f = __fadd_ru(idem2f, __shfl_xor_sync(0xffffffffu, idem2f, o));
         }
+        // the rare float64 parts, and the trace, only where a lane holds one
+        if (__any_sync(0xffffffffu, fro2 != 0.0 || idem2 != 0.0 || tr != 0.0)) {
+            for (int o = 16; o > 0; o >>= 1) {
+                fro2 += __shfl_xor_sync(0xffffffffu, fro2, o);
+                tr += __shfl_xor_sync(0xffffffffu, tr, o);
+                idem2 += __shfl_xor_sync(0xffffffffu, idem2, o);
+            }
+        }
+        fro2 += (double)fro2f;
+        idem2 += (double)idem2f;
         if (lane == 0) {
             red[ew * 3 + 0] = fro2;
             red[ew * 3 + 1] = tr;
@@ -1041,7 +1145,7 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
     }
     tc::fence_before();
     __syncthreads();
-    if (tid < 4 && !a.raw_out) {
+    if (tid < 4 && !a.raw_out && !a.out_int) {
         // block q = 2h + c of the tile: the four epilogue warps whose lane quarter has
         // half h and whose column group has block column c, in warp order
         const int q = tid, hq = q >> 1, cq = q & 1;
@@ -1305,9 +1409,9 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
         ta.status = &sc->status;
         SP_CUDA(cudaMemsetAsync(&sc->status, 0, sizeof(int32_t), s));
         cudaEventRecord(ctx->ev[EV_PLAN1], s);
-        // passes over levels 6..min(L, 9), 10..L, then 2..min(L, 5); the first ones
-        // leave their raw products in the output slots, each later one adds them, and
-        // the last (the largest terms) runs the SP2 epilogue
+        // passes over levels 6..min(L, 9), 10..L, then 2..min(L, 5); the earlier ones
+        // leave their partial products in the output slots, each later one adds them,
+        // and the last (the largest terms) runs the SP2 epilogue
         int ranges[3][2];
         int npass = 0;
         if (lmax >= 6) {
@@ -1329,8 +1433,14 @@ int mixed_plan_and_gemm(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, 
             // exact f32 window: per leaf product a level sum is below 2^18 max(hi + 1, 4)
             const double per = ldexp(1.0, 18) * (hi + 1 > 4 ? hi + 1 : 4);
             ta.window = (int)floor((ldexp(1.0, 24) - 1.0) / per);
-            ta.raw_out = ps + 1 < npass ? 1 : 0;
-            ta.add_prev = ps > 0 ? 1 : 0;
+            // the first pass of several hands its raw int64 sums to the next, which adds
+            // them exactly; a middle pass (levels 10..L) leaves a float64 partial that the
+            // last pass adds
+            ta.out_int = (npass > 1 && ps == 0) ? 1 : 0;
+            ta.prev_int = ps == 1 ? 1 : 0;
+            ta.prev_hi = ranges[0][1];
+            ta.raw_out = (ps + 1 < npass && ps > 0) ? 1 : 0;
+            ta.add_prev = ps > 1 ? 1 : 0;
             ++ctx->launches;
             k.fn<<<(unsigned)n_work, GM_THREADS, k.smem, s>>>(ta);
             SP_CHECK_LAUNCH();
