@@ -502,6 +502,7 @@ namespace spamm {
 void ctx_release(spamm_ctx* c) {
     if (!c || !c->closed || c->refs > 0) return;
     cudaSetDevice(c->device);
+    dcache_release(c->stream);
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 12; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);

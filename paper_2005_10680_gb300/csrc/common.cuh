@@ -108,6 +108,7 @@ struct DevScalars {
 // allocation helpers (stream-ordered pool)
 int dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
+void dcache_release(cudaStream_t s);   // kept large buffers of s back to the pool
 
 int mat_alloc(spamm_ctx* ctx, int64_t n, int bs, int64_t cap, spamm_mat** out);
 void ctx_release(spamm_ctx* ctx);   // frees a closed context once no matrix refers to it
@@ -144,6 +145,48 @@ struct ChargeData {
     const float* tnB = nullptr;
 };
 
+// Conversions between a non-negative float64 and float32 from their bits: the
+// charge is evaluated for every leaf of every Algorithm 3 evaluation, and on GB300
+// the float64 pipe, which the conversion instructions use, is far slower than the
+// integer one. Both give exactly what the conversion instructions give.
+
+// x >= 0 rounded upward to float32
+__device__ __forceinline__ float f64_to_f32_ru_nonneg(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    if (b == 0ull) return 0.f;
+    const int ef = (int)(b >> 52);
+    if (ef == 0x7FF) return __uint_as_float((b & 0xFFFFFFFFFFFFFull) ? 0x7FC00000u : 0x7F800000u);
+    const int e = ef - 1023;                      // x in [2^e, 2^(e + 1)) when normal
+    if (e > 127) return __uint_as_float(0x7F800000u);
+    if (e >= -126) {
+        unsigned int fb = ((unsigned int)(e + 127) << 23) | (unsigned int)((b >> 29) & 0x7FFFFFu);
+        if (b & 0x1FFFFFFFull) fb += 1u;          // may carry into the exponent (or to inf)
+        return __uint_as_float(fb);
+    }
+    if (e < -150) return __uint_as_float(1u);     // below 2^-150 (or a subnormal double)
+    // a multiple of 2^-149 (a subnormal float32, or 2^-126), rounded up
+    const unsigned long long M = (1ull << 52) | (b & 0xFFFFFFFFFFFFFull);
+    const int sh = -97 - e;                       // 30..53
+    unsigned int q = (unsigned int)(M >> sh);
+    if (M & ((1ull << sh) - 1ull)) q += 1u;
+    return __uint_as_float(q);
+}
+
+// float32 c >= 0 to float64, exactly
+__device__ __forceinline__ double f32_to_f64_nonneg(float c) {
+    const unsigned int u = __float_as_uint(c);
+    const unsigned int ef = u >> 23, m = u & 0x7FFFFFu;
+    if (ef == 0xFFu) return __longlong_as_double(m ? 0x7FF8000000000000ll : 0x7FF0000000000000ll);
+    if (ef != 0u)
+        return __longlong_as_double(
+            (long long)(((unsigned long long)(ef + 896u) << 52) | ((unsigned long long)m << 29)));
+    if (m == 0u) return 0.0;
+    const int msb = 31 - __clz((int)m);           // m 2^-149, leading bit at msb
+    return __longlong_as_double(
+        (long long)(((unsigned long long)(msb + 874) << 52) |
+                    (((unsigned long long)m << (52 - msb)) & 0xFFFFFFFFFFFFFull)));
+}
+
 __device__ __forceinline__ double charge(const ChargeData& ch, int32_t sa, int32_t sb,
                                          double norm_b) {
     const int L = ch.lmax;
@@ -151,10 +194,10 @@ __device__ __forceinline__ double charge(const ChargeData& ch, int32_t sa, int32
     const float* snA = ch.snA + (int64_t)sa * MX_SLICES;
     const float* tnA = ch.tnA + (int64_t)sa * MX_SLICES;
     const float* tnB = ch.tnB + (int64_t)sb * MX_SLICES;
-    float c = __fmul_ru(tnA[m - 1], __double2float_ru(norm_b));
+    float c = __fmul_ru(tnA[m - 1], f64_to_f32_ru_nonneg(norm_b));
     for (int p = 1; p <= m; ++p)
         c = __fmaf_ru(snA[p - 1], tnB[(L - p < MX_SLICES ? L - p : MX_SLICES) - 1], c);
-    return (double)c;
+    return f32_to_f64_nonneg(c);
 }
 
 // slot of the B operand's slices for triple (i, k, j)

@@ -10,7 +10,8 @@
 #include <atomic>
 #include <cstdarg>
 #include <cstring>
-
+#include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "common.cuh"
@@ -37,6 +38,82 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
 // k >= 0, the allocation after k more successful ones fails (once).
 static std::atomic<long long> g_fail_after{-1};
 
+// Large buffers (the slices' pair tiles, the tile storage of a product) change size
+// a little from one SP2 step to the next. A request of that kind that no free block
+// of the stream-ordered pool fits grows the pool, which maps new memory (tens of ms
+// for tens of GB), and a large freed block is later split by smaller requests. So
+// freed large buffers are kept whole, per stream, and handed out again to a later
+// request on the same stream that they fit (stream order makes the reuse safe);
+// their capacities carry 1/8 headroom, so that a slightly larger request of the next
+// step still fits. The kept buffers go back to the pool when a request fails for
+// lack of memory, and when the context that uses the stream is released.
+namespace {
+constexpr size_t BIG_MIN = 64ull << 20;   // requests from 64 MB up
+constexpr size_t BIG_KEEP = 8;            // kept buffers, over all streams
+struct BigBuf {
+    void* p;
+    size_t cap;
+    cudaStream_t s;
+};
+std::mutex g_big_mu;
+std::vector<BigBuf> g_big_free;                 // kept, not in use
+std::unordered_map<void*, size_t> g_big_live;   // handed out: their capacities
+
+// give every kept buffer (of stream s, or of all streams) back to the pool
+void big_release(bool all, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(g_big_mu);
+    for (size_t i = 0; i < g_big_free.size();) {
+        if (all || g_big_free[i].s == s) {
+            cudaFreeAsync(g_big_free[i].p, g_big_free[i].s);
+            g_big_free[i] = g_big_free.back();
+            g_big_free.pop_back();
+        } else {
+            ++i;
+        }
+    }
+}
+
+int big_alloc(void** p, size_t bytes, cudaStream_t s) {
+    {
+        std::lock_guard<std::mutex> lock(g_big_mu);
+        size_t best = g_big_free.size();
+        for (size_t i = 0; i < g_big_free.size(); ++i) {
+            const BigBuf& b = g_big_free[i];
+            if (b.s == s && b.cap >= bytes && b.cap / 2 <= bytes &&
+                (best == g_big_free.size() || b.cap < g_big_free[best].cap))
+                best = i;
+        }
+        if (best < g_big_free.size()) {
+            *p = g_big_free[best].p;
+            g_big_live[*p] = g_big_free[best].cap;
+            g_big_free[best] = g_big_free.back();
+            g_big_free.pop_back();
+            return SPAMM_OK;
+        }
+    }
+    size_t cap = bytes + bytes / 8;
+    cap = (cap + (2u << 20) - 1) & ~(size_t)((2u << 20) - 1);
+    cudaError_t e = cudaMallocAsync(p, cap, s);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        big_release(true, s);
+        e = cudaMallocAsync(p, cap, s);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            cap = bytes;
+            e = cudaMallocAsync(p, cap, s);
+        }
+    }
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
+    }
+    std::lock_guard<std::mutex> lock(g_big_mu);
+    g_big_live[*p] = cap;
+    return SPAMM_OK;
+}
+}  // namespace
+
 int dalloc(void** p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
     if (g_fail_after.load(std::memory_order_relaxed) >= 0 && g_fail_after.fetch_sub(1) == 0) {
@@ -44,14 +121,36 @@ int dalloc(void** p, size_t bytes, cudaStream_t s) {
         return SPAMM_ENOMEM;
     }
     if (bytes == 0) bytes = 16;
+    if (bytes >= BIG_MIN) return big_alloc(p, bytes, s);
     cudaError_t e = cudaMallocAsync(p, bytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync", __FILE__, __LINE__);
     return SPAMM_OK;
 }
 
 void dfree(void* p, cudaStream_t s) {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    {
+        std::lock_guard<std::mutex> lock(g_big_mu);
+        auto it = g_big_live.find(p);
+        if (it != g_big_live.end()) {
+            g_big_free.push_back(BigBuf{p, it->second, s});
+            g_big_live.erase(it);
+            if (g_big_free.size() > BIG_KEEP) {
+                // keep the largest: return the smallest kept buffer to the pool
+                size_t m = 0;
+                for (size_t i = 1; i < g_big_free.size(); ++i)
+                    if (g_big_free[i].cap < g_big_free[m].cap) m = i;
+                cudaFreeAsync(g_big_free[m].p, g_big_free[m].s);
+                g_big_free[m] = g_big_free.back();
+                g_big_free.pop_back();
+            }
+            return;
+        }
+    }
+    cudaFreeAsync(p, s);
 }
+
+void dcache_release(cudaStream_t s) { big_release(false, s); }
 
 // ------------------------------------------------------------------ scans
 

@@ -132,10 +132,10 @@ __global__ void k_exponents(const unsigned long long* __restrict__ rmax, const i
 // digits are read off V + C, C = 64 sum_{q<8} 128^q: its low 56 bits hold the
 // digits d_p + 64 (p >= 2) in plain base 128, so every digit (and every tail
 // R_p = sum_{q>p} d_q 2^(7 (9 - q)) = (low 7 (9 - p) bits) - C_p) is computed
-// independently of the others. Slice norms are exact (digit squares summed exactly
-// per row in f32); tail norms are upper bounds: |R_p| per entry (converted to f32
-// rounded up), plus 1/2 where the rounding of V was inexact, summed in f32 and
-// inflated by 2^-12 to cover the f32 rounding. transpose: slice the transposed block with column exponents. The digits
+// independently of the others. Slice norms: digit squares summed exactly per row
+// in f32, rows weighted and summed rounding upward; tail norms: |R_p| per entry plus
+// 1/2 where the rounding of V was inexact, summed in f32 and inflated by 2^-12 to
+// cover that rounding. Both are upper bounds, stored as float32 rounded up. transpose: slice the transposed block with column exponents. The digits
 // go to the block's half of its pair tile.
 constexpr unsigned long long M56 = (1ull << 56) - 1;
 
@@ -237,162 +237,228 @@ __device__ __forceinline__ double pow2_exact(int e) {
                                      : ldexp(1.0, e);
 }
 
-__global__ void __launch_bounds__(256, 3)
-k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int nb, int transpose,
-        const int32_t* __restrict__ expo, uint8_t* __restrict__ pairs,
+// 2^(2 (e - E)) for e <= E as a float32: exact down to 2^-126, 2^-126 below (an
+// overestimate, for upper bounds)
+__device__ __forceinline__ float row_weight(int e, int E) {
+    const int k = 2 * (e - E);
+    return __int_as_float((127 + (k < -126 ? -126 : k)) << 23);
+}
+
+// x 2^k rounded upward (x >= 0), in float32 steps that each round upward
+__device__ __forceinline__ float scale_pow2_ru(float x, int k) {
+    while (k < -126) {
+        x = __fmul_ru(x, 0x1p-126f);
+        k += 126;
+    }
+    while (k > 127) {
+        x = __fmul_ru(x, 0x1p127f);
+        k -= 127;
+    }
+    return __fmul_ru(x, __int_as_float((127 + k) << 23));
+}
+
+// A CTA walks the blocks s = blockIdx.x, + gridDim.x, ...: while it slices one block,
+// the next one streams into the other half of a double buffer (16-byte asynchronous
+// copies, rows padded to SPLIT_LD doubles so that the reads below hit every bank pair
+// at most twice per warp).
+constexpr int SPLIT_LD = 66;
+constexpr int SPLIT_CTAS_PER_SM = 3;
+constexpr size_t SPLIT_SMEM = 2 * MX_BS * SPLIT_LD * sizeof(double);
+
+__device__ __forceinline__ void split_prefetch(double* buf, const double* G, int t) {
+    const char* g = reinterpret_cast<const char*>(G);
+#pragma unroll
+    for (int q = t; q < MX_BS * MX_BS / 2; q += 256) {   // 16-byte pieces: row q >> 5
+        const uint32_t dst = tc::smem_u32(buf + (q >> 5) * SPLIT_LD + 2 * (q & 31));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g + 16 * q)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(256, SPLIT_CTAS_PER_SM)
+k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int64_t nslots,
+        int nb, int transpose, const int32_t* __restrict__ expo, uint8_t* __restrict__ pairs,
         const int64_t* __restrict__ pair_idx, int8_t* __restrict__ p0, float* __restrict__ sn,
         float* __restrict__ tn) {
-    const int64_t s = blockIdx.x;
     const int t = threadIdx.x;
-    __shared__ double T[MX_BS][MX_BS + 1];
+    extern __shared__ __align__(16) double split_buf[];   // [2][MX_BS][SPLIT_LD]
     __shared__ float row_a[MX_BS][MX_S], row_r[MX_BS][MX_S];   // per-row sums
     __shared__ int row_e[MX_BS];
     __shared__ int first;
-    const int32_t cd = coord[s];
-    if (t == 0) first = MX_S + 1;
-    const double* G = tiles + s * MX_BS * MX_BS;
-    for (int e = t; e < MX_BS * MX_BS; e += 256) {
-        const int r = e / MX_BS, c = e % MX_BS;
-        if (transpose) T[c][r] = G[e];
-        else T[r][c] = G[e];
-    }
-    __syncthreads();
-    if (cd < 0) return;
-    const int bi = cd / nb, bj = cd % nb;
-    const int base = (transpose ? bj : bi) * MX_BS;
-    const int row = t >> 2, kq = t & 3;           // kq: two groups of 8 K values each
-    const int e_r = expo[base + row];
-    float sa[MX_S], sr[MX_S];                     // per-thread sums of d_p^2 and (|R_p| + 1/2)^2
+    int64_t s = blockIdx.x;
+    if (s < nslots) split_prefetch(split_buf, tiles + s * MX_BS * MX_BS, t);
+    for (int it = 0; s < nslots; s += gridDim.x, ++it) {
+        const double* T = split_buf + (it & 1) * MX_BS * SPLIT_LD;
+        const int64_t nx = s + gridDim.x;
+        if (nx < nslots) {
+            split_prefetch(split_buf + ((it + 1) & 1) * MX_BS * SPLIT_LD,
+                           tiles + nx * MX_BS * MX_BS, t);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        if (t == 0) first = MX_S + 1;
+        __syncthreads();
+        const int32_t cd = coord[s];
+        if (cd >= 0) {
+            const int bi = cd / nb, bj = cd % nb;
+            const int base = (transpose ? bj : bi) * MX_BS;
+            const int row = t >> 2, kq = t & 3;           // kq: K groups kq and kq + 4 of 8 values
+            const int e_r = expo[base + row];
+            float sa[MX_S], sr[MX_S];                     // per-thread sums of d_p^2 and (|R_p| + 1/2)^2
 #pragma unroll
-    for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.f;
-    // pairing along block rows (transpose = 0) or block columns (transpose = 1)
-    const int pr = transpose ? bj : bi, pk = transpose ? bi : bj;
-    uint8_t* pout =
-        pairs + pair_idx[(int64_t)(pr >> 1) * nb + pk] * (int64_t)PAIR_BYTES + (pr & 1) * CHUNK;
-    unsigned nz = 0u;                             // bit p: some entry has a nonzero digit p + 1
+            for (int p = 0; p < MX_S; ++p) sa[p] = sr[p] = 0.f;
+            // pairing along block rows (transpose = 0) or block columns (transpose = 1)
+            const int pr = transpose ? bj : bi, pk = transpose ? bi : bj;
+            uint8_t* pout =
+                pairs + pair_idx[(int64_t)(pr >> 1) * nb + pk] * (int64_t)PAIR_BYTES + (pr & 1) * CHUNK;
+            unsigned nz = 0u;                             // bit p: some entry has a nonzero digit p + 1
 #pragma unroll 1
-    for (int g2 = 0; g2 < 2; ++g2) {
-        const int kg = kq * 2 + g2;                // 0..7: K columns 8kg..8kg+7
-        uint32_t pk[MX_S][4];                      // bf16 pairs of the 8 values, per slice
+            for (int g2 = 0; g2 < 2; ++g2) {
+                const int kg = g2 * 4 + kq;                // 0..7: K columns 8kg..8kg+7
+                uint32_t pk[MX_S][4];                      // bf16 pairs of the 8 values, per slice
 #pragma unroll
-        for (int p = 0; p < MX_S; ++p) pk[p][0] = pk[p][1] = pk[p][2] = pk[p][3] = 0u;
+                for (int p = 0; p < MX_S; ++p) pk[p][0] = pk[p][1] = pk[p][2] = pk[p][3] = 0u;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            // exact fixed point V = round(x 2^(63 - e_r)) from the bits of x
-            const long long bits = __double_as_longlong(T[row][kg * 8 + e]);
-            const int ex = (int)((bits >> 52) & 0x7FF);
-            long long m = bits & 0xFFFFFFFFFFFFFll;
-            int E;
-            if (ex == 0) {
-                E = -1074;
-            } else {
-                m |= 1ll << 52;
-                E = ex - 1075;
-            }
-            const int sh = E + 7 * MX_S - e_r;     // V = m 2^sh
-            long long V;
-            bool inexact = false;                  // V != x 2^(63 - e_r)
-            if (m == 0) V = 0;
-            else if (sh >= 0) V = m << sh;         // |x| < 2^e_r keeps this below 2^63
-            else if (sh > -63) {
-                V = (m + (1ll << (-sh - 1))) >> (-sh);
-                inexact = (m & ((1ll << (-sh)) - 1)) != 0;
-            } else {
-                V = 0;
-                inexact = true;
-            }
-            if (bits < 0) V = -V;
-            const float half = inexact ? 0.5f : 0.f;
-            // V = hi 2^56 + lo, lo in [0, 2^56); lo + C = carry 2^56 + L with L the digits + 64
-            const unsigned long long tt = ((unsigned long long)V & M56) + digit_offset(8);
-            const unsigned int Llo = (unsigned int)tt, Lhi = (unsigned int)(tt >> 32) & 0xFFFFFFu;
-            const int d1 = (int)(V >> 56) + (int)(tt >> 56);
-            int d[MX_S];
-            d[0] = d1;
+                for (int e = 0; e < 8; ++e) {
+                    // exact fixed point V = round(x 2^(63 - e_r)) from the bits of x
+                    const int col = kg * 8 + e;
+                    const long long bits = __double_as_longlong(
+                        transpose ? T[col * SPLIT_LD + row] : T[row * SPLIT_LD + col]);
+                    const int ex = (int)((bits >> 52) & 0x7FF);
+                    long long m = bits & 0xFFFFFFFFFFFFFll;
+                    int E;
+                    if (ex == 0) {
+                        E = -1074;
+                    } else {
+                        m |= 1ll << 52;
+                        E = ex - 1075;
+                    }
+                    const int sh = E + 7 * MX_S - e_r;     // V = m 2^sh
+                    long long V;
+                    bool inexact = false;                  // V != x 2^(63 - e_r)
+                    if (m == 0) V = 0;
+                    else if (sh >= 0) V = m << sh;         // |x| < 2^e_r keeps this below 2^63
+                    else if (sh > -63) {
+                        V = (m + (1ll << (-sh - 1))) >> (-sh);
+                        inexact = (m & ((1ll << (-sh)) - 1)) != 0;
+                    } else {
+                        V = 0;
+                        inexact = true;
+                    }
+                    if (bits < 0) V = -V;
+                    const float half = inexact ? 0.5f : 0.f;
+                    // V = hi 2^56 + lo, lo in [0, 2^56); lo + C = carry 2^56 + L with L the digits + 64
+                    const unsigned long long tt = ((unsigned long long)V & M56) + digit_offset(8);
+                    const unsigned int Llo = (unsigned int)tt, Lhi = (unsigned int)(tt >> 32) & 0xFFFFFFu;
+                    const int d1 = (int)(V >> 56) + (int)(tt >> 56);
+                    int d[MX_S];
+                    d[0] = d1;
 #pragma unroll
-            for (int p = 1; p < MX_S; ++p) {       // digit p + 1 sits at bits 7 (8 - p)
-                const int at = MX_W * (MX_S - 1 - p);
-                unsigned int f;
-                if (at + 7 <= 32) f = (Llo >> at) & 127u;
-                else if (at >= 32) f = (Lhi >> (at - 32)) & 127u;
-                else f = __funnelshift_r(Llo, Lhi, at) & 127u;
-                d[p] = (int)f - 64;
-            }
-            // tails from the bottom: R_8 = d_9, R_p = d_(p+1) 128^(8 - p) + R_(p+1). Each
-            // step is one rounding of a sum whose magnitude is at least half of its
-            // larger term (balanced digits), so the relative error of |R_p| stays below
-            // 2^-21, inside the 2^-12 inflation of the tail norms
-            float r = 0.f;
+                    for (int p = 1; p < MX_S; ++p) {       // digit p + 1 sits at bits 7 (8 - p)
+                        const int at = MX_W * (MX_S - 1 - p);
+                        unsigned int f;
+                        if (at + 7 <= 32) f = (Llo >> at) & 127u;
+                        else if (at >= 32) f = (Lhi >> (at - 32)) & 127u;
+                        else f = __funnelshift_r(Llo, Lhi, at) & 127u;
+                        d[p] = (int)f - 64;
+                    }
+                    // tails from the bottom: R_8 = d_9, R_p = d_(p+1) 128^(8 - p) + R_(p+1). Each
+                    // step is one rounding of a sum whose magnitude is at least half of its
+                    // larger term (balanced digits), so the relative error of |R_p| stays below
+                    // 2^-21, inside the 2^-12 inflation of the tail norms
+                    float r = 0.f;
 #pragma unroll
-            for (int p = MX_S - 1; p >= 0; --p) {  // slice p + 1
-                const float fd = small_int_to_float(d[p]);   // exact: |d| <= 128
-                sa[p] = fmaf(fd, fd, sa[p]);
-                nz |= (d[p] != 0 ? 1u : 0u) << p;
-                // bf16 of an integer of at most 8 significant bits: the top half of its
-                // float32 bits, exactly
-                pk[p][e >> 1] |= (__float_as_uint(fd) >> 16) << (16 * (e & 1));
-                if (p < MX_S - 1) {
-                    // tail after digit p + 1 (units of 2^(e_r - 63)): r holds R_(p+1)
-                    const float rf = fabsf(r) + half;
-                    sr[p] = fmaf(rf, rf, sr[p]);
+                    for (int p = MX_S - 1; p >= 0; --p) {  // slice p + 1
+                        const float fd = small_int_to_float(d[p]);   // exact: |d| <= 128
+                        sa[p] = fmaf(fd, fd, sa[p]);
+                        nz |= (d[p] != 0 ? 1u : 0u) << p;
+                        // bf16 of an integer of at most 8 significant bits: the top half of its
+                        // float32 bits, exactly
+                        pk[p][e >> 1] |= (__float_as_uint(fd) >> 16) << (16 * (e & 1));
+                        if (p < MX_S - 1) {
+                            // tail after digit p + 1 (units of 2^(e_r - 63)): r holds R_(p+1)
+                            const float rf = fabsf(r) + half;
+                            sr[p] = fmaf(rf, rf, sr[p]);
+                        }
+                        // weight of digit p + 1: 128^(8 - p) = 2^(7 (8 - p)), an exact float32
+                        if (p > 0) r = fmaf(fd, __int_as_float((127 + MX_W * (MX_S - 1 - p)) << 23), r);
+                    }
+                    sr[MX_S - 1] += half * half;           // tail after all digits: |T_S| <= 1/2 unit
                 }
-                // weight of digit p + 1: 128^(8 - p) = 2^(7 (8 - p)), an exact float32
-                if (p > 0) r = fmaf(fd, __int_as_float((127 + MX_W * (MX_S - 1 - p)) << 23), r);
+#pragma unroll
+                for (int p = 0; p < MX_S; ++p) {
+                    const int within = (row >> 3) * 256 + (kg & 1) * 128 + (row & 7) * 16;
+                    const uint4 v = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
+                    *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
+                }
             }
-            sr[MX_S - 1] += half * half;           // tail after all digits: |T_S| <= 1/2 unit
-        }
+            const int firstp = nz ? __ffs((int)nz) : MX_S + 1;
+            // per-row sums over the row's 4 lanes, in f32: exact for the digit squares (integers
+            // below 2^24), covered by the 2^-12 inflation for the tails
 #pragma unroll
-        for (int p = 0; p < MX_S; ++p) {
-            const int within = (row >> 3) * 256 + (kg & 1) * 128 + (row & 7) * 16;
-            const uint4 v = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
-            *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
-        }
-    }
-    const int firstp = nz ? __ffs((int)nz) : MX_S + 1;
-    // per-row sums over the row's 4 lanes, in f32: exact for the digit squares (integers
-    // below 2^24), covered by the 2^-12 inflation for the tails
-#pragma unroll
-    for (int p = 0; p < MX_S; ++p) {
-        sa[p] += __shfl_xor_sync(0xffffffffu, sa[p], 1);
-        sa[p] += __shfl_xor_sync(0xffffffffu, sa[p], 2);
-        sr[p] += __shfl_xor_sync(0xffffffffu, sr[p], 1);
-        sr[p] += __shfl_xor_sync(0xffffffffu, sr[p], 2);
-    }
-    if (kq == 0) {
-#pragma unroll
-        for (int p = 0; p < MX_S; ++p) {
-            row_a[row][p] = sa[p];
-            row_r[row][p] = sr[p];
-        }
-        row_e[row] = e_r;
-    }
-    atomicMin(&first, firstp);
-    __syncthreads();
-    // rows scaled by 2^(2 (e_r - 7p)) (slice p) or 2^(2 (e_r - 63)) (tails) and summed in
-    // float64: warp 0 the slices, warp 1 the tails, two rows per lane
-    const int warp = t >> 5, lane = t & 31;
-    if (warp < 2) {
-        const int e0 = row_e[lane], e1 = row_e[lane + 32];
-#pragma unroll
-        for (int p = 0; p < MX_S; ++p) {
-            double v;
-            if (warp == 0)
-                v = (double)row_a[lane][p] * pow2_exact(2 * (e0 - MX_W * (p + 1))) +
-                    (double)row_a[lane + 32][p] * pow2_exact(2 * (e1 - MX_W * (p + 1)));
-            else
-                v = (double)row_r[lane][p] * pow2_exact(2 * (e0 - MX_W * MX_S)) +
-                    (double)row_r[lane + 32][p] * pow2_exact(2 * (e1 - MX_W * MX_S));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            // float32 rounded up, after a 2^-40 margin for the float64 sums and root
-            if (lane == 0) {
-                if (warp == 0) sn[s * MX_S + p] = __double2float_ru(sqrt(v) * (1.0 + 0x1p-40));
-                else tn[s * MX_S + p] =
-                    __double2float_ru(sqrt(v * (1.0 + 0x1p-12)) * (1.0 + 0x1p-40));
+            for (int p = 0; p < MX_S; ++p) {
+                sa[p] += __shfl_xor_sync(0xffffffffu, sa[p], 1);
+                sa[p] += __shfl_xor_sync(0xffffffffu, sa[p], 2);
+                sr[p] += __shfl_xor_sync(0xffffffffu, sr[p], 1);
+                sr[p] += __shfl_xor_sync(0xffffffffu, sr[p], 2);
             }
+            if (kq == 0) {
+#pragma unroll
+                for (int p = 0; p < MX_S; ++p) {
+                    row_a[row][p] = sa[p];
+                    row_r[row][p] = sr[p];
+                }
+                row_e[row] = e_r;
+            }
+            atomicMin(&first, firstp);
+            __syncthreads();
+            // rows scaled by 2^(2 (e_r - 7p)) (slice p) or 2^(2 (e_r - 63)) (tails) and summed:
+            // warp 0 the slices, warp 1 the tails, two rows per lane. Relative to the largest
+            // exponent E of a non-zero row, every row's weight 2^(2 (e_r - E)) <= 1 is a
+            // float32 (2^-126 for rows more than 63 binades below, an overestimate), and the
+            // sums, roots and the final scaling by 2^(E - 7p) or 2^(E - 63) round upward:
+            // upper bounds, off the slow float64 pipe.
+            const int warp = t >> 5, lane = t & 31;
+            if (warp < 2) {
+                const int e0 = row_e[lane], e1 = row_e[lane + 32];
+                // a row with a non-zero entry has a non-zero digit, or an inexact rounding
+                // (the last tail sum); e_r is its matrix row's exponent, not the block's
+                float any0 = row_r[lane][MX_S - 1], any1 = row_r[lane + 32][MX_S - 1];
+#pragma unroll
+                for (int p = 0; p < MX_S; ++p) {
+                    any0 += row_a[lane][p];
+                    any1 += row_a[lane + 32][p];
+                }
+                const bool live0 = any0 > 0.f, live1 = any1 > 0.f;
+                int E = max(live0 ? e0 : INT_MIN, live1 ? e1 : INT_MIN);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) E = max(E, __shfl_xor_sync(0xffffffffu, E, o));
+                const float w0 = live0 ? row_weight(e0, E) : 0.f, w1 = live1 ? row_weight(e1, E) : 0.f;
+#pragma unroll
+                for (int p = 0; p < MX_S; ++p) {
+                    float v = warp == 0 ? __fmaf_ru(row_a[lane][p], w0, __fmul_ru(row_a[lane + 32][p], w1))
+                                        : __fmaf_ru(row_r[lane][p], w0, __fmul_ru(row_r[lane + 32][p], w1));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+                    if (lane == 0) {
+                        if (E == INT_MIN) {
+                            (warp == 0 ? sn : tn)[s * MX_S + p] = 0.f;
+                        } else if (warp == 0) {
+                            sn[s * MX_S + p] = scale_pow2_ru(__fsqrt_ru(v), E - MX_W * (p + 1));
+                        } else {
+                            // the tails' float32 sums are inflated by 2^-12 for their rounding
+                            tn[s * MX_S + p] =
+                                scale_pow2_ru(__fsqrt_ru(__fmul_ru(v, 1.0f + 0x1p-12f)), E - MX_W * MX_S);
+                        }
+                    }
+                }
+            }
+            if (t == 0) p0[s] = (int8_t)first;
         }
+        __syncthreads();   // this buffer and the row sums are free for the next blocks
     }
-    if (t == 0) p0[s] = (int8_t)first;
 }
 
 struct SliceSet {
@@ -477,6 +543,21 @@ __global__ void k_pair_zero_missing(const int32_t* __restrict__ map, int nb, int
 
 // Slices of X into pair tiles: pairs of block rows, or of block columns when
 // transpose (the right operand, sliced with column exponents).
+static bool g_split_attr[64] = {false};
+static std::mutex g_split_init;
+
+static int split_attributes(spamm_ctx* ctx) {
+    std::lock_guard<std::mutex> lock(g_split_init);
+    if (ctx->device < 0 || ctx->device >= 64) return SPAMM_EINVAL;
+    if (g_split_attr[ctx->device]) return SPAMM_OK;
+    SP_CUDA(cudaFuncSetAttribute(k_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SPLIT_SMEM));
+    // all of the unified L1 / shared-memory array as shared memory: three CTAs per SM
+    SP_CUDA(cudaFuncSetAttribute(k_split, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    g_split_attr[ctx->device] = true;
+    return SPAMM_OK;
+}
+
 static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, SliceSet* out) {
     cudaStream_t s = ctx->stream;
     const int64_t ns = X->nslots > 0 ? X->nslots : 1;
@@ -530,9 +611,12 @@ static int split_matrix(spamm_ctx* ctx, const spamm_mat* X, int transpose, Slice
                                                                out->expo);
     if (X->nslots > 0) {
         ++ctx->launches;
-        k_split<<<(unsigned)X->nslots, 256, 0, s>>>(X->d_tiles, X->d_coord, X->nb, transpose,
-                                                    out->expo, out->pairs, out->pair_idx,
-                                                    out->p0, out->sn, out->tn);
+        SP_TRY(split_attributes(ctx));
+        const int64_t resident = (int64_t)SPLIT_CTAS_PER_SM * ctx->num_sms;
+        const unsigned grid = (unsigned)(X->nslots < resident ? X->nslots : resident);
+        k_split<<<grid, 256, SPLIT_SMEM, s>>>(X->d_tiles, X->d_coord, X->nslots, X->nb, transpose,
+                                              out->expo, out->pairs, out->pair_idx, out->p0,
+                                              out->sn, out->tn);
     }
     SP_CHECK_LAUNCH();
     lists.free(s);
@@ -770,6 +854,7 @@ constexpr int GM_THREADS = 18 * 32;   // warp 0 copies, warp 1 issues MMAs, 16 f
 constexpr int MAX_LEVELS = 4;         // 4 levels x 128 columns = all 512 TMEM columns
 constexpr long long WAIT_LIMIT = 1ll << 22;
 constexpr int SMEM_BUDGET = 220 * 1024;
+constexpr int ACC_LD = 513;           // epilogue: stride of one column of the staged sums
 
 // Stage layout of a pass over levels LO..HI: the slices 1..SMAX of the A and of the B
 // pair tile for one K chunk, each [slice][half][2 KB] (the M = 128 and N = 128
@@ -827,7 +912,7 @@ template <int LO, int HI>
 __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
     using PS = PassShape<LO, HI>;
     static_assert(HI - LO < MAX_LEVELS && LO >= 2 && HI <= 2 * MX_S, "levels must fit in TMEM");
-    static_assert(PS::NST * PS::STAGE >= 512 * 32 * 8, "the epilogue stages its sums in the ring");
+    static_assert(PS::NST * PS::STAGE >= 32 * ACC_LD * 8, "the epilogue stages its sums in the ring");
     constexpr int SMAX = PS::SMAX, HALF = PS::HALF, STAGE = PS::STAGE, NST = PS::NST;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* stages = smem;
@@ -1044,49 +1129,59 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
         }
         // ---- values, SP2 combination, writes, partial sums
         // Every MMA and bulk copy of this tile has completed (the last window was
-        // waited for), so the stage ring is free: the sums move there, one slot per
-        // column and thread (conflict-free), and the loop below keeps few registers.
+        // waited for), so the stage ring is free. Each warp holds a 32 x 32 square of
+        // the tile (rows 32 quarter + lane, columns 32 cb + j) and turns it over in
+        // its own part of the ring: lane i's column j at j * ACC_LD + 32 ew + i (an
+        // odd stride, so that both sweeps read without bank conflicts). Sweep 1 walks
+        // the square by rows, the lanes along the row, so every global access is one
+        // coalesced 256-byte run, and leaves each output value in its sum's slot;
+        // sweep 2 writes the mirror block (the transposed copy) with the lanes along
+        // its rows, again in 256-byte runs.
         long long* accs = reinterpret_cast<long long*>(stages);
         const int et = tid - 64;                  // 0..511
 #pragma unroll
-        for (int j = 0; j < 32; ++j) accs[j * 512 + et] = acc[j];
+        for (int j = 0; j < 32; ++j) accs[j * ACC_LD + et] = acc[j];
+        __syncwarp();
         const int nb = a.nb;
         const int32_t ij = a.work_ij[w];
         const int I = ij / a.np, J = ij % a.np;
-        const int rl = quarter * 32 + lane;      // 0..127
-        const int h = rl >> 6, rr = rl & 63;
-        const int cc = cb >> 1, sc0 = (cb & 1) * 32;
+        const int h = quarter >> 1, cc = cb >> 1, sc = (cb & 1) * 32 + lane;
         const int bi = 2 * I + h, bj = 2 * J + cc;
+        const int src = ew * 32;                  // row i of the square: slots lane * ACC_LD + src + i
         // squared norms: float32 rounded up (upper bounds) for entries below 2^56, a
         // float64 sum for larger ones
         float fro2f = 0.f, idem2f = 0.f;
         double fro2 = 0.0, tr = 0.0, idem2 = 0.0;
-        if (bi < nb && bj < nb) {
+        long long dg = 0;                         // bits of the lane's diagonal entry
+        const bool inside = bi < nb && bj < nb;
+        if (inside) {
             const int32_t os = a.work_out[8 * w + 2 * h + cc];
-            const int32_t ost = a.work_out[8 * w + 4 + 2 * h + cc];
-            const int er = a.expA[bi * MX_BS + rr];
+            const int r0 = 32 * (quarter & 1);    // first row of the square within block bi
+            const int er_lane = a.expA[bi * MX_BS + r0 + lane];
+            const int fs = a.expB[bj * MX_BS + sc];
             const double* X = nullptr;
             if (a.mode != 0 && a.mapX) {
                 const int32_t xs = a.mapX[(int64_t)bi * nb + bj];
                 if (xs >= 0) X = a.tilesX + (int64_t)xs * MX_BS * MX_BS;
             }
             double* Co = os >= 0 ? a.tilesC + (int64_t)os * MX_BS * MX_BS : nullptr;
-            double* Ct = ost >= 0 ? a.tilesC + (int64_t)ost * MX_BS * MX_BS : nullptr;
 #pragma unroll 2
-            for (int j = 0; j < 32; ++j) {
-                const int sc = sc0 + j;
-                const int fs = a.expB[bj * MX_BS + sc];
-                const long long aj = accs[j * 512 + et];
+            for (int i = 0; i < 32; ++i) {
+                const int rr = r0 + i;
+                const int er = __shfl_sync(0xffffffffu, er_lane, i);
+                long long* slot = accs + lane * ACC_LD + src + i;
+                const long long aj = *slot;
+                const int at = rr * MX_BS + sc;
                 if (a.out_int) {
                     // raw int64 sums, for the last pass to combine exactly
-                    if (Co) reinterpret_cast<long long*>(Co)[rr * MX_BS + sc] = aj;
+                    if (Co) reinterpret_cast<long long*>(Co)[at] = aj;
                     continue;
                 }
                 // V 2^e, correctly rounded, built from the integer's bits; with the raw
                 // sums of an earlier pass the two are first added exactly in 128 bits
                 double cv;
                 if (a.prev_int && Co) {
-                    const long long vp = reinterpret_cast<const long long*>(Co)[rr * MX_BS + sc];
+                    const long long vp = reinterpret_cast<const long long*>(Co)[at];
                     const int hmax = HI > a.prev_hi ? HI : a.prev_hi;
                     const __int128 t =
                         HI > a.prev_hi
@@ -1096,31 +1191,46 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
                 } else {
                     cv = i64_scaled_to_double(aj, er + fs - MX_W * HI);
                 }
-                if (a.add_prev && Co) cv += Co[rr * MX_BS + sc];
+                if (a.add_prev && Co) cv += Co[at];
                 if (a.raw_out) {
-                    if (Co) Co[rr * MX_BS + sc] = cv;
+                    if (Co) Co[at] = cv;
                     continue;
                 }
-                const double x = X ? X[rr * MX_BS + sc] : 0.0;
+                const double x = X ? X[at] : 0.0;
                 const double out = a.mode == 2 ? 2.0 * x - cv : cv;
-                if (a.mode != 0) {
-                    const double dcx = cv - x;
-                    if (f32_square_safe(dcx)) {
-                        const float f = abs_f64_to_f32_ru(dcx);
-                        idem2f = __fmaf_ru(f, f, idem2f);
-                    } else {
+                // the float64 work is kept out of the common path: a predicated float64
+                // instruction still takes its turn on the slow float64 pipe, so the
+                // rare large entries are summed behind a warp vote
+                const double dcx = a.mode != 0 ? cv - x : 0.0;
+                const bool rare = !f32_square_safe(out) || !f32_square_safe(dcx);
+                if (__any_sync(0xffffffffu, rare)) {
+                    if (rare) {
+                        fro2 = fma(out, out, fro2);
                         idem2 = fma(dcx, dcx, idem2);
                     }
                 }
-                if (f32_square_safe(out)) {
-                    const float f = abs_f64_to_f32_ru(out);
+                if (!rare) {
+                    const float f = abs_f64_to_f32_ru(out), g = abs_f64_to_f32_ru(dcx);
                     fro2f = __fmaf_ru(f, f, fro2f);
-                } else {
-                    fro2 = fma(out, out, fro2);
+                    idem2f = __fmaf_ru(g, g, idem2f);
                 }
-                if (bi == bj && rr == sc) tr += out;
-                if (Co) Co[rr * MX_BS + sc] = out;
-                if (Ct) Ct[sc * MX_BS + rr] = out;
+                // the one diagonal entry of a lane (diagonal blocks): kept, added after
+                if (bi == bj && rr == sc) dg = __double_as_longlong(out);
+                if (Co) Co[at] = out;
+                *slot = __double_as_longlong(out);
+            }
+        }
+        tr = __longlong_as_double(dg);
+        if (!a.out_int && !a.raw_out) {
+            // sweep 2: the mirror block, lanes along its rows (the tile's columns)
+            __syncwarp();
+            const int32_t ost = inside ? a.work_out[8 * w + 4 + 2 * h + cc] : -1;
+            if (ost >= 0) {
+                double* Ct = a.tilesC + (int64_t)ost * MX_BS * MX_BS;
+                const int rr = 32 * (quarter & 1) + lane, sc0 = (cb & 1) * 32;
+#pragma unroll 4
+                for (int j = 0; j < 32; ++j)
+                    Ct[(sc0 + j) * MX_BS + rr] = __longlong_as_double(accs[j * ACC_LD + et]);
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
