@@ -355,8 +355,8 @@ def per_purification(sums_ms, world, steps):
 # ---------------------------------------------------------------- peaks
 
 def load_peaks():
-    """MEASURED_PEAKS.json when present (measured on this machine), else the profiling
-    recipe's fallback figures."""
+    """MEASURED_PEAKS.json when present (peaks measured on this GPU model: a copy and
+    a bf16 GEMM), else fixed fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         p = json.load(open(path))
@@ -570,6 +570,9 @@ def run_ours(args, rank, world):
     return 0
 
 
+GEMM_DRAM_BYTES_PER_PIPE_FLOP = None   # set from the capture below
+
+
 def purification_summary(args, B, reps, rep0, form):
     """The roofline of the dominant kernel, the phase split, the step logs and the
     checks of one bench configuration's purifications."""
@@ -594,7 +597,19 @@ def purification_summary(args, B, reps, rep0, form):
                 "algorithmic": "2*128*128*64 flop per (p,q) bf16 slice pair of a 128x128 tile "
                                "task (4 MMAs of 128x128x16)"}
     achieved = pipe / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else 0.0
-    roof.update({"achieved": achieved, "frac": achieved / roof["peak"], "traffic": None})
+    traffic = None
+    if form != "fp64":
+        # DRAM bytes of the leaf-product kernel per issued slice-pair flop, from one
+        # ncu capture of both passes of an SP2 product of the n = 65536 lattice; the
+        # bytes are the pair tiles copied, so they grow with the pairs formed, and the
+        # figure is scaled to this run's average launch by its pipe flops
+        passes = lambda L: 1 + (L >= 6) + (L >= 10)
+        launches = sum(sum(passes(L) for L in r["step_lmax"]) + passes(r["step_lmax"][-1])
+                       for r in reps if r["step_lmax"])
+        if launches and GEMM_DRAM_BYTES_PER_PIPE_FLOP is not None:
+            traffic = GEMM_DRAM_BYTES_PER_PIPE_FLOP * pipe / launches
+    roof.update({"achieved": achieved, "frac": achieved / roof["peak"], "traffic": traffic,
+                 "traffic_unit": "bytes per launch (average launch)"})
     nb2 = (B.n // bs) ** 2
     phase = lambda q: sum(r["ms_phase"][q] for r in reps) / K
     return {

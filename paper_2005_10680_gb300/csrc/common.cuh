@@ -150,9 +150,17 @@ struct ChargeData {
 // the float64 pipe, which the conversion instructions use, is far slower than the
 // integer one. Both give exactly what the conversion instructions give.
 
+// The bits of a float64, opaque to the compiler: tests and orders written on the bits
+// are otherwise turned back into float64 compares, which run on the slow float64 pipe.
+__device__ __forceinline__ unsigned long long f64_bits(double x) {
+    unsigned long long r;
+    asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+    return r;
+}
+
 // x >= 0 rounded upward to float32
 __device__ __forceinline__ float f64_to_f32_ru_nonneg(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long b = f64_bits(x);
     if (b == 0ull) return 0.f;
     const int ef = (int)(b >> 52);
     if (ef == 0x7FF) return __uint_as_float((b & 0xFFFFFFFFFFFFFull) ? 0x7FC00000u : 0x7F800000u);

@@ -81,7 +81,7 @@ __device__ __forceinline__ double fold_levels(double* sh, int levels) {
 // non-negative finite values (norms, their products, tau) the integer order of the
 // bits is the order of the values, and the integer pipe is far faster on GB300 than
 // the float64 one that compares and fmax would use. The results are bit-identical.
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ long long dbits(double x) { return (long long)f64_bits(x); }
 __device__ __forceinline__ double dmax_nn(double a, double b) { return dbits(a) >= dbits(b) ? a : b; }
 
 // Algorithm 3's leaf term for the triple (i, k, j) at threshold tau (0 outside the

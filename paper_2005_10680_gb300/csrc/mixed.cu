@@ -212,7 +212,7 @@ __device__ __forceinline__ double i128_scaled_to_double(__int128 v, int ex) {
 // |x| as float32 rounded up, from its bits; only for |x| < 2^56 (the caller checks),
 // below 2^-126 it returns 2^-126 (or 0 for 0)
 __device__ __forceinline__ float abs_f64_to_f32_ru(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long b = f64_bits(x) & 0x7FFFFFFFFFFFFFFFull;
     const int ef = (int)(b >> 52) - 1023 + 127;
     if (ef <= 0) return b == 0ull ? 0.f : 1.17549435e-38f;
     unsigned int fb = ((unsigned int)ef << 23) | ((unsigned int)(b >> 29) & 0x7FFFFFu);
@@ -222,7 +222,7 @@ __device__ __forceinline__ float abs_f64_to_f32_ru(double x) {
 
 // |x| < 2^56: its square, and a sum of 4096 such squares, stay inside float32
 __device__ __forceinline__ bool f32_square_safe(double x) {
-    return ((unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull) <
+    return (f64_bits(x) & 0x7FFFFFFFFFFFFFFFull) <
            0x4370000000000000ull;   // 2^56
 }
 
@@ -324,7 +324,7 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                 for (int e = 0; e < 8; ++e) {
                     // exact fixed point V = round(x 2^(63 - e_r)) from the bits of x
                     const int col = kg * 8 + e;
-                    const long long bits = __double_as_longlong(
+                    const long long bits = (long long)f64_bits(
                         transpose ? T[col * SPLIT_LD + row] : T[row * SPLIT_LD + col]);
                     const int ex = (int)((bits >> 52) & 0x7FF);
                     long long m = bits & 0xFFFFFFFFFFFFFll;
@@ -855,6 +855,7 @@ constexpr int MAX_LEVELS = 4;         // 4 levels x 128 columns = all 512 TMEM c
 constexpr long long WAIT_LIMIT = 1ll << 22;
 constexpr int SMEM_BUDGET = 220 * 1024;
 constexpr int ACC_LD = 513;           // epilogue: stride of one column of the staged sums
+constexpr int EPI_G = 4;              // epilogue: rows whose loads are issued together
 
 // Stage layout of a pass over levels LO..HI: the slices 1..SMAX of the A and of the B
 // pair tile for one K chunk, each [slice][half][2 KB] (the M = 128 and N = 128
@@ -949,6 +950,25 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
 
     if (warp == 0) {
         // -------------------------------------------- producer (whole warp)
+        // First the blocks the epilogue will read (the earlier pass's sums in the
+        // output slots, the blocks of X) go to L2, where they wait out this tile's
+        // products instead of costing the epilogue an HBM round trip per row.
+        if (lane < 8) {
+            const int32_t ij = a.work_ij[w];
+            const int q = lane & 3, bi = 2 * (ij / a.np) + (q >> 1), bj = 2 * (ij % a.np) + (q & 1);
+            const double* blk = nullptr;
+            if (bi < a.nb && bj < a.nb) {
+                if (lane < 4) {
+                    const int32_t os = a.work_out[8 * w + q];
+                    if ((a.prev_int || a.add_prev) && os >= 0)
+                        blk = a.tilesC + (int64_t)os * MX_BS * MX_BS;
+                } else if (a.mode != 0 && a.mapX && !a.out_int && !a.raw_out) {
+                    const int32_t xs = a.mapX[(int64_t)bi * a.nb + bj];
+                    if (xs >= 0) blk = a.tilesX + (int64_t)xs * MX_BS * MX_BS;
+                }
+            }
+            if (blk) tc::bulk_prefetch_l2(blk, MX_BS * MX_BS * sizeof(double));
+        }
         // lanes load the metadata of 32 tasks at a time; per stage lane 0 copies the
         // A slices pa..pmax and lane 1 the B slices qb..qmax, each one contiguous run
         int it = 0;
@@ -966,6 +986,29 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
                 const int32_t jA = __shfl_sync(0xffffffffu, pA, j);
                 const int32_t jB = __shfl_sync(0xffffffffu, pB, j);
                 const int jpq = __shfl_sync(0xffffffffu, pq, j);
+                {
+                    // the next task's slices into L2 now, a task (4 stages) ahead of
+                    // its copies: most copies then land from L2 instead of waiting on
+                    // HBM, while the ring holds only 3 stages. Lane c takes A's K chunk
+                    // c, lane 4 + c B's.
+                    const int jn = (j + 1) & 31;
+                    const int32_t nA = __shfl_sync(0xffffffffu, pA, jn);
+                    const int32_t nB = __shfl_sync(0xffffffffu, pB, jn);
+                    const int npq = __shfl_sync(0xffffffffu, pq, jn);
+                    if (j + 1 < cnt && task_active<HI>(npq) && lane < 2 * KCH) {
+                        const int na = npq & 0xff, nq = npq >> 8;
+                        const int c = lane & (KCH - 1);
+                        const bool isA = lane < KCH;
+                        const int lo = isA ? na : nq;
+                        const int hi = min(SMAX, HI - (isA ? nq : na));
+                        if (hi >= lo)
+                            tc::bulk_prefetch_l2(
+                                (isA ? a.pairA + (int64_t)nA * PAIR_BYTES
+                                     : a.pairB + (int64_t)nB * PAIR_BYTES) +
+                                    (lo - 1) * 2 * CHUNK + c * PAIR_CSTRIDE,
+                                (uint32_t)(hi - lo + 1) * 2 * CHUNK);
+                    }
+                }
                 if (!task_active<HI>(jpq)) continue;
                 const int pa = jpq & 0xff, qb = jpq >> 8;
                 const int pmax = min(SMAX, HI - qb), qmax = min(SMAX, HI - pa);
@@ -1165,59 +1208,70 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
                 if (xs >= 0) X = a.tilesX + (int64_t)xs * MX_BS * MX_BS;
             }
             double* Co = os >= 0 ? a.tilesC + (int64_t)os * MX_BS * MX_BS : nullptr;
-#pragma unroll 2
-            for (int i = 0; i < 32; ++i) {
-                const int rr = r0 + i;
-                const int er = __shfl_sync(0xffffffffu, er_lane, i);
-                long long* slot = accs + lane * ACC_LD + src + i;
-                const long long aj = *slot;
-                const int at = rr * MX_BS + sc;
-                if (a.out_int) {
-                    // raw int64 sums, for the last pass to combine exactly
-                    if (Co) reinterpret_cast<long long*>(Co)[at] = aj;
-                    continue;
+            const double* Xe = a.out_int || a.raw_out ? nullptr : X;   // read by the epilogue
+            // rows in groups of EPI_G: the group's global loads are issued together
+            for (int i0 = 0; i0 < 32; i0 += EPI_G) {
+                long long vpg[EPI_G];
+                double xg[EPI_G];
+#pragma unroll
+                for (int u = 0; u < EPI_G; ++u) {
+                    const int at = (r0 + i0 + u) * MX_BS + sc;
+                    vpg[u] = (a.prev_int && Co) ? reinterpret_cast<const long long*>(Co)[at] : 0;
+                    xg[u] = Xe ? Xe[at] : 0.0;
                 }
-                // V 2^e, correctly rounded, built from the integer's bits; with the raw
-                // sums of an earlier pass the two are first added exactly in 128 bits
-                double cv;
-                if (a.prev_int && Co) {
-                    const long long vp = reinterpret_cast<const long long*>(Co)[at];
-                    const int hmax = HI > a.prev_hi ? HI : a.prev_hi;
-                    const __int128 t =
-                        HI > a.prev_hi
-                            ? (__int128)aj + ((__int128)vp << (MX_W * (HI - a.prev_hi)))
-                            : (__int128)vp + ((__int128)aj << (MX_W * (a.prev_hi - HI)));
-                    cv = i128_scaled_to_double(t, er + fs - MX_W * hmax);
-                } else {
-                    cv = i64_scaled_to_double(aj, er + fs - MX_W * HI);
-                }
-                if (a.add_prev && Co) cv += Co[at];
-                if (a.raw_out) {
-                    if (Co) Co[at] = cv;
-                    continue;
-                }
-                const double x = X ? X[at] : 0.0;
-                const double out = a.mode == 2 ? 2.0 * x - cv : cv;
-                // the float64 work is kept out of the common path: a predicated float64
-                // instruction still takes its turn on the slow float64 pipe, so the
-                // rare large entries are summed behind a warp vote
-                const double dcx = a.mode != 0 ? cv - x : 0.0;
-                const bool rare = !f32_square_safe(out) || !f32_square_safe(dcx);
-                if (__any_sync(0xffffffffu, rare)) {
-                    if (rare) {
-                        fro2 = fma(out, out, fro2);
-                        idem2 = fma(dcx, dcx, idem2);
+#pragma unroll
+                for (int u = 0; u < EPI_G; ++u) {
+                    const int i = i0 + u;
+                    const int rr = r0 + i;
+                    const int er = __shfl_sync(0xffffffffu, er_lane, i);
+                    long long* slot = accs + lane * ACC_LD + src + i;
+                    const long long aj = *slot;
+                    const int at = rr * MX_BS + sc;
+                    if (a.out_int) {
+                        // raw int64 sums, for the last pass to combine exactly
+                        if (Co) reinterpret_cast<long long*>(Co)[at] = aj;
+                        continue;
                     }
+                    // V 2^e, correctly rounded, built from the integer's bits; with the raw
+                    // sums of an earlier pass the two are first added exactly in 128 bits
+                    double cv;
+                    if (a.prev_int && Co) {
+                        const long long vp = vpg[u];
+                        const int hmax = HI > a.prev_hi ? HI : a.prev_hi;
+                        const __int128 t =
+                            HI > a.prev_hi
+                                ? (__int128)aj + ((__int128)vp << (MX_W * (HI - a.prev_hi)))
+                                : (__int128)vp + ((__int128)aj << (MX_W * (a.prev_hi - HI)));
+                        cv = i128_scaled_to_double(t, er + fs - MX_W * hmax);
+                    } else {
+                        cv = i64_scaled_to_double(aj, er + fs - MX_W * HI);
+                    }
+                    if (a.add_prev && Co) cv += Co[at];
+                    if (a.raw_out) {
+                        if (Co) Co[at] = cv;
+                        continue;
+                    }
+                    const double x = xg[u];
+                    const double out = a.mode == 2 ? 2.0 * x - cv : cv;
+                    // entries beyond 2^56 (rare) are summed in float64, behind a warp vote
+                    const double dcx = a.mode != 0 ? cv - x : 0.0;
+                    const bool rare = !f32_square_safe(out) || !f32_square_safe(dcx);
+                    if (__any_sync(0xffffffffu, rare)) {
+                        if (rare) {
+                            fro2 = fma(out, out, fro2);
+                            idem2 = fma(dcx, dcx, idem2);
+                        }
+                    }
+                    if (!rare) {
+                        const float f = abs_f64_to_f32_ru(out), g = abs_f64_to_f32_ru(dcx);
+                        fro2f = __fmaf_ru(f, f, fro2f);
+                        idem2f = __fmaf_ru(g, g, idem2f);
+                    }
+                    // the one diagonal entry of a lane (diagonal blocks): kept, added after
+                    if (bi == bj && rr == sc) dg = __double_as_longlong(out);
+                    if (Co) Co[at] = out;
+                    *slot = __double_as_longlong(out);
                 }
-                if (!rare) {
-                    const float f = abs_f64_to_f32_ru(out), g = abs_f64_to_f32_ru(dcx);
-                    fro2f = __fmaf_ru(f, f, fro2f);
-                    idem2f = __fmaf_ru(g, g, idem2f);
-                }
-                // the one diagonal entry of a lane (diagonal blocks): kept, added after
-                if (bi == bj && rr == sc) dg = __double_as_longlong(out);
-                if (Co) Co[at] = out;
-                *slot = __double_as_longlong(out);
             }
         }
         tr = __longlong_as_double(dg);

@@ -74,6 +74,12 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
         : "memory");
 }
 
+// 1-D bulk prefetch of global memory into L2 (bytes % 16 == 0, 16-byte aligned): no
+// shared memory, no completion to wait for.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 // Shared-memory matrix descriptor (tcgen05): K-major, no swizzle, core matrices of
 // 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo = along M/N.
 __device__ __forceinline__ uint64_t desc_kmajor(uint32_t addr, uint32_t lbo, uint32_t sbo) {
