@@ -570,7 +570,11 @@ def run_ours(args, rank, world):
     return 0
 
 
-GEMM_DRAM_BYTES_PER_PIPE_FLOP = None   # set from the capture below
+# DRAM bytes of the leaf-product kernel per issued slice-pair flop: one ncu capture of
+# both passes of the third SP2 product of the n = 65536 lattice (levels 6..9: 41.77 +
+# 4.55 GB read + written, levels 2..5: 13.54 + 9.03 GB; 68.90 GB), over that run's
+# average pipe flops per product (784.28 TFLOP/s x 394.1 ms / 13 products = 2.378e13)
+GEMM_DRAM_BYTES_PER_PIPE_FLOP = 68.90e9 / 2.378e13
 
 
 def purification_summary(args, B, reps, rep0, form):

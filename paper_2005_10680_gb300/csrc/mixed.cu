@@ -265,13 +265,16 @@ constexpr int SPLIT_LD = 66;
 constexpr int SPLIT_CTAS_PER_SM = 3;
 constexpr size_t SPLIT_SMEM = 2 * MX_BS * SPLIT_LD * sizeof(double);
 
-__device__ __forceinline__ void split_prefetch(double* buf, const double* G, int t) {
+// the slots of blocks that truncation removed (coord < 0) are not read
+__device__ __forceinline__ void split_prefetch(double* buf, const double* G, bool live, int t) {
     const char* g = reinterpret_cast<const char*>(G);
+    if (live) {
 #pragma unroll
-    for (int q = t; q < MX_BS * MX_BS / 2; q += 256) {   // 16-byte pieces: row q >> 5
-        const uint32_t dst = tc::smem_u32(buf + (q >> 5) * SPLIT_LD + 2 * (q & 31));
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g + 16 * q)
-                     : "memory");
+        for (int q = t; q < MX_BS * MX_BS / 2; q += 256) {   // 16-byte pieces: row q >> 5
+            const uint32_t dst = tc::smem_u32(buf + (q >> 5) * SPLIT_LD + 2 * (q & 31));
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(g + 16 * q)
+                         : "memory");
+        }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -287,13 +290,13 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
     __shared__ int row_e[MX_BS];
     __shared__ int first;
     int64_t s = blockIdx.x;
-    if (s < nslots) split_prefetch(split_buf, tiles + s * MX_BS * MX_BS, t);
+    if (s < nslots) split_prefetch(split_buf, tiles + s * MX_BS * MX_BS, coord[s] >= 0, t);
     for (int it = 0; s < nslots; s += gridDim.x, ++it) {
         const double* T = split_buf + (it & 1) * MX_BS * SPLIT_LD;
         const int64_t nx = s + gridDim.x;
         if (nx < nslots) {
             split_prefetch(split_buf + ((it + 1) & 1) * MX_BS * SPLIT_LD,
-                           tiles + nx * MX_BS * MX_BS, t);
+                           tiles + nx * MX_BS * MX_BS, coord[nx] >= 0, t);
             asm volatile("cp.async.wait_group 1;" ::: "memory");
         } else {
             asm volatile("cp.async.wait_group 0;" ::: "memory");
