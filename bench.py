@@ -571,10 +571,10 @@ def run_ours(args, rank, world):
 
 
 # DRAM bytes of the leaf-product kernel per issued slice-pair flop: one ncu capture of
-# both passes of the third SP2 product of the n = 65536 lattice (levels 6..9: 41.77 +
-# 4.55 GB read + written, levels 2..5: 13.54 + 9.03 GB; 68.90 GB), over that run's
-# average pipe flops per product (784.28 TFLOP/s x 394.1 ms / 13 products = 2.378e13)
-GEMM_DRAM_BYTES_PER_PIPE_FLOP = 68.90e9 / 2.378e13
+# both passes of the third SP2 product of the n = 65536 lattice (levels 6..9: 39.29 +
+# 4.55 GB read + written, levels 2..5: 13.47 + 9.03 GB; 66.34 GB), over that run's
+# average pipe flops per product (796.7 TFLOP/s x 387.9 ms / 13 products = 2.377e13)
+GEMM_DRAM_BYTES_PER_PIPE_FLOP = 66.34e9 / 2.377e13
 
 
 def purification_summary(args, B, reps, rep0, form):

@@ -989,29 +989,6 @@ __global__ void __launch_bounds__(GM_THREADS, 1) k_gemm_tile(TileArgs a) {
                 const int32_t jA = __shfl_sync(0xffffffffu, pA, j);
                 const int32_t jB = __shfl_sync(0xffffffffu, pB, j);
                 const int jpq = __shfl_sync(0xffffffffu, pq, j);
-                {
-                    // the next task's slices into L2 now, a task (4 stages) ahead of
-                    // its copies: most copies then land from L2 instead of waiting on
-                    // HBM, while the ring holds only 3 stages. Lane c takes A's K chunk
-                    // c, lane 4 + c B's.
-                    const int jn = (j + 1) & 31;
-                    const int32_t nA = __shfl_sync(0xffffffffu, pA, jn);
-                    const int32_t nB = __shfl_sync(0xffffffffu, pB, jn);
-                    const int npq = __shfl_sync(0xffffffffu, pq, jn);
-                    if (j + 1 < cnt && task_active<HI>(npq) && lane < 2 * KCH) {
-                        const int na = npq & 0xff, nq = npq >> 8;
-                        const int c = lane & (KCH - 1);
-                        const bool isA = lane < KCH;
-                        const int lo = isA ? na : nq;
-                        const int hi = min(SMAX, HI - (isA ? nq : na));
-                        if (hi >= lo)
-                            tc::bulk_prefetch_l2(
-                                (isA ? a.pairA + (int64_t)nA * PAIR_BYTES
-                                     : a.pairB + (int64_t)nB * PAIR_BYTES) +
-                                    (lo - 1) * 2 * CHUNK + c * PAIR_CSTRIDE,
-                                (uint32_t)(hi - lo + 1) * 2 * CHUNK);
-                    }
-                }
                 if (!task_active<HI>(jpq)) continue;
                 const int pa = jpq & 0xff, qb = jpq >> 8;
                 const int pmax = min(SMAX, HI - qb), qmax = min(SMAX, HI - pa);
