@@ -66,17 +66,25 @@ __global__ void k_block_rowmax(const double* __restrict__ tiles, const int32_t* 
         return;
     }
     if (!transpose) {
-        // warp w takes half rows w, w + 8, ...: 32 consecutive entries per load
+        // warp w takes half rows w, w + 8, ...: 32 consecutive entries per load, all
+        // 16 loads of a thread issued before the reductions
         const int w = t >> 5, lane = t & 31;
         unsigned long long* hm = &sh[0][0];      // [128] half-row maxima
-        for (int hr = w; hr < 2 * MX_BS; hr += 8) {
-            unsigned long long v = T[(hr >> 1) * MX_BS + (hr & 1) * 32 + lane] & ABS;
+        unsigned long long x[2 * MX_BS / 8];
+#pragma unroll
+        for (int i = 0; i < 2 * MX_BS / 8; ++i) {
+            const int hr = w + 8 * i;
+            x[i] = T[(hr >> 1) * MX_BS + (hr & 1) * 32 + lane] & ABS;
+        }
+#pragma unroll
+        for (int i = 0; i < 2 * MX_BS / 8; ++i) {
+            unsigned long long v = x[i];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
                 v = u > v ? u : v;
             }
-            if (lane == 0) hm[hr] = v;
+            if (lane == 0) hm[w + 8 * i] = v;
         }
         __syncthreads();
         if (t < 64) {
