@@ -131,8 +131,8 @@ __global__ void k_exponents(const unsigned long long* __restrict__ rmax, const i
     expo[r] = e;
 }
 
-// One CTA (256 threads) per stored block: digits, leading-zero slice, slice and
-// tail norms, in integer arithmetic. With |x| < 2^e_r, V = x 2^(63 - e_r) is
+// Per stored block (a CTA of 256 threads at a time, 4 threads per row): digits,
+// leading-zero slice, slice and tail norms, in integer arithmetic. With |x| < 2^e_r, V = x 2^(63 - e_r) is
 // rounded to an int64 (the rounding is the last tail, at most half a unit) and
 // cut into balanced base-128 digits,
 //     V = d_1 2^56 + sum_{p=2..9} d_p 2^(7 (9 - p)),  d_p in [-64, 63] for p >= 2,
@@ -143,8 +143,9 @@ __global__ void k_exponents(const unsigned long long* __restrict__ rmax, const i
 // independently of the others. Slice norms: digit squares summed exactly per row
 // in f32, rows weighted and summed rounding upward; tail norms: |R_p| per entry plus
 // 1/2 where the rounding of V was inexact, summed in f32 and inflated by 2^-12 to
-// cover that rounding. Both are upper bounds, stored as float32 rounded up. transpose: slice the transposed block with column exponents. The digits
-// go to the block's half of its pair tile.
+// cover that rounding. Both are upper bounds, stored as float32 rounded up.
+// transpose: slice the transposed block with column exponents. The digits go to the
+// block's half of its pair tile.
 constexpr unsigned long long M56 = (1ull << 56) - 1;
 
 __host__ __device__ constexpr unsigned long long digit_offset(int low_digits) {
@@ -324,13 +325,11 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
             const int pr = transpose ? bj : bi, pk = transpose ? bi : bj;
             uint8_t* pout =
                 pairs + pair_idx[(int64_t)(pr >> 1) * nb + pk] * (int64_t)PAIR_BYTES + (pr & 1) * CHUNK;
-            unsigned nz = 0u;                             // bit p: some entry has a nonzero digit p + 1
 #pragma unroll 1
             for (int g2 = 0; g2 < 2; ++g2) {
                 const int kg = g2 * 4 + kq;                // 0..7: K columns 8kg..8kg+7
                 uint32_t pk[MX_S][4];                      // bf16 pairs of the 8 values, per slice
-#pragma unroll
-                for (int p = 0; p < MX_S; ++p) pk[p][0] = pk[p][1] = pk[p][2] = pk[p][3] = 0u;
+                float fev[MX_S];                           // digits of the pair's even entry
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     // exact fixed point V = round(x 2^(63 - e_r)) from the bits of x
@@ -384,10 +383,13 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                     for (int p = MX_S - 1; p >= 0; --p) {  // slice p + 1
                         const float fd = small_int_to_float(d[p]);   // exact: |d| <= 128
                         sa[p] = fmaf(fd, fd, sa[p]);
-                        nz |= (d[p] != 0 ? 1u : 0u) << p;
                         // bf16 of an integer of at most 8 significant bits: the top half of its
-                        // float32 bits, exactly
-                        pk[p][e >> 1] |= (__float_as_uint(fd) >> 16) << (16 * (e & 1));
+                        // float32 bits, exactly; two entries' halves per 32-bit word
+                        if (e & 1)
+                            pk[p][e >> 1] =
+                                __byte_perm(__float_as_uint(fev[p]), __float_as_uint(fd), 0x7632);
+                        else
+                            fev[p] = fd;
                         if (p < MX_S - 1) {
                             // tail after digit p + 1 (units of 2^(e_r - 63)): r holds R_(p+1)
                             const float rf = fabsf(r) + half;
@@ -405,6 +407,11 @@ k_split(const double* __restrict__ tiles, const int32_t* __restrict__ coord, int
                     *reinterpret_cast<uint4*>(pout + (kg >> 1) * PAIR_CSTRIDE + p * 2 * CHUNK + within) = v;
                 }
             }
+            // bit p: some entry of this thread has a nonzero digit p + 1 (its exact
+            // sum of squared digits is positive)
+            unsigned nz = 0u;
+#pragma unroll
+            for (int p = 0; p < MX_S; ++p) nz |= (sa[p] > 0.f ? 1u : 0u) << p;
             const int firstp = nz ? __ffs((int)nz) : MX_S + 1;
             // per-row sums over the row's 4 lanes, in f32: exact for the digit squares (integers
             // below 2^24), covered by the 2^-12 inflation for the tails
