@@ -240,12 +240,6 @@ __device__ __forceinline__ float small_int_to_float(int d) {
     return __int_as_float(0x4B400000 + d) - 12582912.0f;
 }
 
-__device__ __forceinline__ double pow2_exact(int e) {
-    // 2^e; a constructed power of two where it is a normal double
-    return (e >= -1022 && e <= 1023) ? __longlong_as_double((long long)(e + 1023) << 52)
-                                     : ldexp(1.0, e);
-}
-
 // 2^(2 (e - E)) for e <= E as a float32: exact down to 2^-126, 2^-126 below (an
 // overestimate, for upper bounds)
 __device__ __forceinline__ float row_weight(int e, int E) {
