@@ -55,6 +55,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     spamm_report r;
     memset(&r, 0, sizeof r);
     cudaEventRecord(ctx->ev[EV_T0], s);
+    NvtxPhases phase("spamm: operand structures and slices");
     // SP2 steps multiply a symmetric X by itself: use a bitwise-symmetric norm map
     // so that the kept set of (j, i) is exactly the transpose of that of (i, j),
     // and form only the blocks i <= j.
@@ -105,6 +106,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
             return st;
         }
         cudaEventRecord(ctx->ev[EV_CSE0], s);
+        phase.enter("spamm: slice levels (Algorithm 3 at tau = 0)");
         // fewest levels whose certified charge (everything formed, tau = 0) stays
         // within half of delta: the charge shrinks as levels are added, so bisect over
         // L in [4, 13]; with a given tau every level up to 10 is formed. At L = 13 the
@@ -163,6 +165,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
             use_mixed = false;
         }
     }
+    phase.enter("spamm: tau search (Algorithm 3)");
     if (st == SPAMM_OK) {
         ChargeData ch = use_mixed ? mixed_charge(A, B, nA, nB, mp, lmax_used) : ChargeData();
         int ev2 = 0;
@@ -179,6 +182,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
         evals += ev2;
     }
     cudaEventRecord(ctx->ev[EV_CSE1], s);
+    phase.enter("spamm: plan and leaf products (Algorithm 2)");
     double* parts = nullptr;
     if (st == SPAMM_OK && use_mixed) {
         int64_t npairs = 0;
@@ -214,6 +218,7 @@ int multiply_core(spamm_ctx* ctx, const spamm_mat* A, const spamm_mat* B, bool s
     dfree(nsym, s);
     release_structs();
     cudaEventRecord(ctx->ev[EV_END], s);
+    phase.enter("spamm: report");
     DevScalars h;
     if (st == SPAMM_OK) {
         cudaError_t e = cudaMemcpyAsync(&h, sc, sizeof h, cudaMemcpyDeviceToHost, s);
@@ -559,6 +564,7 @@ extern "C" int spamm_truncate(spamm_ctx* ctx, spamm_mat* X, double delta, int sy
         return SPAMM_EINVAL;
     }
     SP_CUDA(cudaSetDevice(ctx->device));
+    NvtxPhases phase("spamm: truncate (Algorithm 1)");
     cudaEventRecord(ctx->ev[EV_TR0], ctx->stream);
     int64_t removed = 0;
     double rsq = 0.0;
@@ -626,6 +632,7 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
     *D = nullptr;
     if (n_occ == 0 || n_occ == F->n) return purify_trivial(ctx, F, n_occ == F->n, D, rep);
     SP_CUDA(cudaSetDevice(ctx->device));
+    NvtxPhases phase("spamm: purify");
     cudaStream_t s = ctx->stream;
     spamm_purify_report R;
     if (rep) R = *rep;
@@ -703,6 +710,7 @@ extern "C" int spamm_purify(spamm_ctx* ctx, const spamm_mat* F, int64_t n_occ, d
             st = SPAMM_EINVAL;
             break;
         }
+        NvtxPhases step(sq ? "spamm: SP2 step X^2" : "spamm: SP2 step 2X - X^2");
         spamm_report mr;
         spamm_mat* Xn = nullptr;
         if (variant == SPAMM_TRUNCMUL)

@@ -6,8 +6,27 @@
 #include <string>
 
 #include "../../include/spamm.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace spamm {
+
+// Named phases for profilers: NVTX ranges (no-ops unless a tool is attached), one
+// open at a time per object and closed on every way out of the scope.
+struct NvtxPhases {
+    bool open = false;
+    void enter(const char* name) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    NvtxPhases() = default;
+    explicit NvtxPhases(const char* name) { enter(name); }
+    NvtxPhases(const NvtxPhases&) = delete;
+    NvtxPhases& operator=(const NvtxPhases&) = delete;
+    ~NvtxPhases() {
+        if (open) nvtxRangePop();
+    }
+};
 
 // ----------------------------------------------------------------- errors
 
