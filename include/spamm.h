@@ -111,7 +111,12 @@ typedef struct {
 /* Create a context on CUDA device `device`. `cuda_stream` is a cudaStream_t
    owned by the caller, or NULL to let the context create (and own) one.
    spamm_destroy may be called while matrices of the context are alive: the
-   context (and its stream) is released when the last of them is freed. */
+   context (and its stream) is released when the last of them is freed.
+   Device memory: every allocation is ordered on the context's stream. Freed
+   buffers of 64 MB and more (tile storage, operand slices) are kept whole, at
+   most 8 in all, for later requests on the same stream that they fit; they go
+   back to the stream-ordered pool when an allocation fails for lack of memory
+   and when the context is released. */
 int spamm_create(spamm_ctx** ctx, int device, void* cuda_stream);
 void spamm_destroy(spamm_ctx* ctx);
 const char* spamm_strerror(int status);
